@@ -1,0 +1,198 @@
+/*
+ * msat.h -- C ABI of the GB300 MaxSAT gradient engine.
+ *
+ * The engine runs the solving loop of torchmSAT (arXiv 2402.03640) on one
+ * GPU.  The problem statement it serves is the paper's (Sec. 2, Eq. 1): a
+ * CNF formula F = c_1 and ... and c_m over n Boolean variables; the answer is
+ * an assignment that leaves as few clauses unsatisfied as possible (the
+ * cost), optionally weighted (an extension the paper lists as future work in
+ * Sec. 6).  Each optimizer step is (Sec. 4, Algorithm 1):
+ *
+ *   t = tanh(x)                         relaxed variables x in R^n
+ *   f_j = sum over literals of c_j of (+t_i for x_i, -t_i for not x_i)
+ *   x'_i = [x_i > 0];  clause j is unsat iff no literal is true under x'
+ *   cost = sum of w_j over unsat clauses  (exact integer)
+ *   best cost / best assignment kept (Alg. 1 lines 5-7)
+ *   L = sum_{unsat j} w_j f_j^2 / sum_{unsat j} w_j    (masked MSE)
+ *   gradient by backpropagation, one Adam step (Sec. 5)
+ *   a restart whose cost reaches 0 stops (Alg. 1 stop rule)
+ *
+ * B independent restarts run side by side ("restarts"); each has its own x,
+ * Adam state, unsat set, loss and best assignment.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative MSAT_E* code; the message of the
+ *     last failure on the calling thread is returned by msat_last_error().
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the GPU that was current when the context was made.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps.  The context owns its device state and frees it in
+ *     msat_destroy().
+ *   - Work is issued on the context's stream.  Calls that return results to
+ *     host buffers synchronise that stream; calls that only touch device
+ *     buffers are asynchronous on it.
+ *   - Floating-point arithmetic is IEEE fp32 with a fixed evaluation order
+ *     (literal / occurrence order, 32-term leaves summed in order, leaves
+ *     combined by the dyadic tree), so results are reproducible run to run.
+ */
+#ifndef MSAT_H
+#define MSAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSAT_OK 0
+#define MSAT_EINVAL (-1)   /* bad argument or malformed CNF                      */
+#define MSAT_ENOMEM (-2)   /* host or device allocation failed                   */
+#define MSAT_EBUDGET (-3)  /* request does not fit the server's memory budget    */
+#define MSAT_ETIMEOUT (-4) /* a bounded device wait gave up                      */
+#define MSAT_ECUDA (-5)    /* a CUDA runtime call failed                         */
+#define MSAT_EAGAIN (-6)   /* result not ready yet (msat_poll)                   */
+#define MSAT_ESTATE (-7)   /* call not valid in the object's current state       */
+
+#define MSAT_BACKEND_SPARSE 0 /* clause CSR gather kernel                       */
+#define MSAT_BACKEND_DENSE 1  /* tensor-core GEMM of the clause matrix          */
+
+typedef struct msat_ctx msat_ctx;
+
+/* Solver settings.  Fill with msat_config_default() and override. */
+typedef struct {
+    double lr;        /* Adam learning rate; the paper uses 1e-4 (Sec. 5)      */
+    double beta1;     /* Adam first-moment decay (default 0.9)                 */
+    double beta2;     /* Adam second-moment decay (default 0.999)              */
+    double eps;       /* Adam epsilon (default 1e-8)                           */
+    int32_t restarts; /* B: 1, 2, 4, ..., 1024 (a power of two)                */
+    int32_t reserved0;
+    uint64_t seed_x;  /* seed of the random start of x (Alg. 1 line 1)         */
+} msat_config;
+
+/* Write the defaults (lr 1e-4, Adam 0.9/0.999/1e-8, B = 1, seed 1). */
+int msat_config_default(msat_config *cfg);
+
+/*
+ * Build a solver context for one CNF (Alg. 1 line 1: "construct W").
+ *   n_vars      n >= 1 (variables are numbered 1..n in lits)
+ *   n_clauses   m >= 0
+ *   clause_off  host int64[m+1], clause j holds lits[clause_off[j] ..
+ *               clause_off[j+1]); clause_off[0] = 0, non-decreasing
+ *   lits        host int32[clause_off[m]], DIMACS literals: +(i+1) for x_i,
+ *               -(i+1) for not x_i; 0 and |l| > n are rejected
+ *   weights     host int64[m] clause weights >= 1, or NULL for all 1
+ *   cfg         settings (NULL = defaults)
+ *   stream      cudaStream_t to issue work on (NULL = the legacy default
+ *               stream)
+ * A literal repeated inside a clause is dropped (W has one entry per
+ * variable and clause); a clause holding x and not x is kept and is never
+ * unsatisfied; an empty clause is always unsatisfied.  Clauses longer than
+ * 1024 literals, nnz >= 2^31 and m or n >= 2^30 are rejected (MSAT_EINVAL).
+ * x is initialised on the device: x[i][b] = k * 2^-23 - 1 with k the top 24
+ * bits of output number b*n + i of the SplitMix64 stream seeded with
+ * seed_x; Adam moments are zero; the best cost starts at sum_j w_j.
+ */
+int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const int64_t *clause_off,
+                const int32_t *lits, const int64_t *weights, const msat_config *cfg,
+                void *stream);
+
+/* Free every resource of the context (NULL is ignored). */
+void msat_destroy(msat_ctx *ctx);
+
+/* Issue later work of this context on another cudaStream_t. */
+int msat_set_stream(msat_ctx *ctx, void *stream);
+
+/*
+ * Run n_steps iterations of Algorithm 1 (evaluate x, keep the best, masked
+ * MSE loss, gradient, one Adam step) and then one evaluation of the final x.
+ *   loss_out   host float[B]: loss at the last updated x, or NULL
+ *   cost_out   host int64[B]: cost of the final x, or NULL
+ * With both outputs NULL the call is asynchronous on the context stream.
+ * n_steps = 0 only evaluates the current x.
+ */
+int msat_step(msat_ctx *ctx, int32_t n_steps, float *loss_out, int64_t *cost_out);
+
+/*
+ * Exact cost of a batch of assignments (Sec. 4, "Unsatisfiable Cores": a
+ * clause is unsatisfied iff x'.W equals -len with x' read as +-1).
+ *   assign_pm1  device int8[n][nb], entry (i, b) at i*nb + b: +1 = true,
+ *               -1 = false (any value > 0 counts as true)
+ *   nb          number of assignments, >= 1
+ *   cost_out    device int64[nb]: sum of w_j over clauses with no true literal
+ *   backend     MSAT_BACKEND_SPARSE or MSAT_BACKEND_DENSE
+ * Asynchronous on the context stream; the result is exact for both
+ * backends.
+ */
+int msat_evaluate(msat_ctx *ctx, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
+                  int32_t backend);
+
+/*
+ * Best assignment and cost seen so far per restart (Alg. 1 lines 5-7).
+ *   assign01   host uint8[B][n] (0/1), or NULL
+ *   best_cost  host int64[B], or NULL
+ */
+int msat_best(msat_ctx *ctx, uint8_t *assign01, int64_t *best_cost);
+
+/* Copy the current relaxed variables to host float[n][B] (entry i*B + b). */
+int msat_get_x(msat_ctx *ctx, float *x_host);
+
+/*
+ * Relaxed objective and its gradient at a caller-supplied x, without an
+ * optimizer step (the differentiable layer of Sec. 4).
+ *   x        device float[n][B]
+ *   loss     device float[B]   (masked MSE per restart)
+ *   cost     device int64[B] or NULL (exact cost of x' = [x > 0])
+ * msat_forward keeps tanh(x), the unsat mask and 2/sum_U w in the context;
+ * msat_backward then writes
+ *   grad     device float[n][B] = dloss/dx, scaled per restart by
+ *   gscale   device float[B] (NULL = all ones),
+ * for the x of the most recent msat_forward on this context.  The mask is
+ * piecewise constant and is not differentiated.  These calls do not touch
+ * the context's own x, Adam state or best assignment.
+ */
+int msat_forward(msat_ctx *ctx, const float *x, float *loss, int64_t *cost);
+int msat_backward(msat_ctx *ctx, const float *gscale, float *grad);
+
+/* Sizes and counters of a context. */
+typedef struct {
+    int32_t n;            /* variables                                         */
+    int32_t restarts;     /* B                                                 */
+    int64_t m;            /* clauses                                           */
+    int64_t nnz;          /* literals after dropping repeats                   */
+    int64_t steps_done;   /* optimizer steps taken                             */
+    int64_t device_bytes; /* device memory held by the context                 */
+    int32_t max_clause_len;
+    int32_t max_degree;   /* most occurrences of one variable                  */
+    int32_t n_heavy;      /* variables whose occurrence sum is split across warps */
+    int32_t uniform_len;  /* common clause length, or 0 if lengths differ      */
+} msat_info;
+
+int msat_get_info(msat_ctx *ctx, msat_info *info);
+
+/*
+ * Checkpoint: the full solver state as plain host arrays, so a resumed run
+ * continues bit for bit.
+ *   x, mom, vel   host float[n][B]
+ *   best_cost     host int64[B]
+ *   best_assign   host uint8[n][B] (0/1, entry i*B + b)
+ *   steps_done    host int64[1]
+ *   adam_pow      host double[2]: beta1^steps_done, beta2^steps_done as the
+ *                 running products the step kernels use
+ * msat_get_state fills them; msat_set_state loads them (any may be NULL in
+ * get; all are required in set).
+ */
+int msat_get_state(msat_ctx *ctx, float *x, float *mom, float *vel, int64_t *best_cost,
+                   uint8_t *best_assign, int64_t *steps_done, double *adam_pow);
+int msat_set_state(msat_ctx *ctx, const float *x, const float *mom, const float *vel,
+                   const int64_t *best_cost, const uint8_t *best_assign, int64_t steps_done,
+                   const double *adam_pow);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *msat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSAT_H */

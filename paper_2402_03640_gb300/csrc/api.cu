@@ -1,0 +1,536 @@
+// C ABI of the MaxSAT gradient engine: context creation (validation, clause
+// canonicalisation, CSR and transposed CSR, device upload), the step loop,
+// evaluation, best assignment, checkpoint and the differentiable probe.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "msat_internal.cuh"
+
+namespace msat {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return MSAT_ECUDA;
+}
+
+}  // namespace msat
+
+using namespace msat;
+
+// Device memory of one context.  Every buffer is a separate allocation so
+// each starts on a 256-byte boundary (vector loads need 16 bytes).
+struct msat_ctx {
+    msat_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int32_t n = 0, B = 0;
+    int64_t m = 0, nnz = 0;
+    int32_t kfix = 0, max_len = 0, max_deg = 0;
+    int64_t wsum = 0;
+    int64_t steps_done_host = 0;
+    std::vector<void *> allocs;
+    int64_t device_bytes = 0;
+
+    DevInst I{};
+    DevState S{};
+    DevStep D{};
+
+    // probe (autograd) path, allocated on first use
+    bool probe_ready = false;
+    DevState PS{};
+    DevStep PD{};
+};
+
+static int dalloc(msat_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(MSAT_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) +
+                                     " bytes failed: " + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    c->device_bytes += (int64_t)bytes;
+    return MSAT_OK;
+}
+
+template <typename T>
+static int dalloc_t(msat_ctx *c, T **p, size_t count) {
+    return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+static void free_all(msat_ctx *c) {
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+extern "C" int msat_config_default(msat_config *cfg) {
+    if (!cfg) return fail(MSAT_EINVAL, "msat_config_default: cfg is NULL");
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->lr = 1e-4;
+    cfg->beta1 = 0.9;
+    cfg->beta2 = 0.999;
+    cfg->eps = 1e-8;
+    cfg->restarts = 1;
+    cfg->seed_x = 1;
+    return MSAT_OK;
+}
+
+extern "C" const char *msat_last_error(void) { return g_last_error.c_str(); }
+
+static bool valid_restarts(int32_t B) {
+    return B >= 1 && B <= 1024 && (B & (B - 1)) == 0;
+}
+
+extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
+                           const int64_t *clause_off, const int32_t *lits, const int64_t *weights,
+                           const msat_config *cfg_in, void *stream) {
+    if (!out) return fail(MSAT_EINVAL, "msat_create: out is NULL");
+    *out = nullptr;
+    msat_config cfg;
+    if (cfg_in) cfg = *cfg_in; else msat_config_default(&cfg);
+    if (n_vars < 1 || n_vars >= (1 << 30))
+        return fail(MSAT_EINVAL, "msat_create: n_vars must be in [1, 2^30)");
+    if (n_clauses < 0 || n_clauses >= (1LL << 30))
+        return fail(MSAT_EINVAL, "msat_create: n_clauses must be in [0, 2^30)");
+    if (!clause_off) return fail(MSAT_EINVAL, "msat_create: clause_off is NULL");
+    if (!valid_restarts(cfg.restarts))
+        return fail(MSAT_EINVAL, "msat_create: restarts must be a power of two in [1, 1024]");
+    if (!(cfg.lr > 0) || !(cfg.beta1 >= 0 && cfg.beta1 < 1) || !(cfg.beta2 >= 0 && cfg.beta2 < 1) ||
+        !(cfg.eps >= 0))
+        return fail(MSAT_EINVAL, "msat_create: Adam settings out of range");
+    const int64_t m = n_clauses;
+    if (clause_off[0] != 0) return fail(MSAT_EINVAL, "msat_create: clause_off[0] must be 0");
+    for (int64_t j = 0; j < m; ++j)
+        if (clause_off[j + 1] < clause_off[j])
+            return fail(MSAT_EINVAL, "msat_create: clause_off is not non-decreasing at clause " +
+                                         std::to_string(j));
+    const int64_t raw = clause_off[m];
+    if (raw > 0 && !lits) return fail(MSAT_EINVAL, "msat_create: lits is NULL");
+    if (raw >= (1LL << 31)) return fail(MSAT_EINVAL, "msat_create: more than 2^31-1 literals");
+    for (int64_t q = 0; q < raw; ++q) {
+        const int32_t l = lits[q];
+        if (l == 0 || l > n_vars || l < -n_vars)
+            return fail(MSAT_EINVAL, "msat_create: literal " + std::to_string(l) + " at position " +
+                                         std::to_string(q) + " is 0 or names no variable");
+    }
+    if (weights)
+        for (int64_t j = 0; j < m; ++j)
+            if (weights[j] < 1)
+                return fail(MSAT_EINVAL, "msat_create: weight of clause " + std::to_string(j) +
+                                             " is below 1");
+
+    // canonical clauses: drop a literal equal to an earlier one of its clause
+    std::vector<int32_t> coff((size_t)m + 1);
+    std::vector<int32_t> lit;
+    lit.reserve((size_t)raw);
+    int64_t wsum = 0;
+    int32_t max_len = 0;
+    coff[0] = 0;
+    for (int64_t j = 0; j < m; ++j) {
+        const size_t start = lit.size();
+        for (int64_t p = clause_off[j]; p < clause_off[j + 1]; ++p) {
+            const int32_t l = lits[p];
+            const int32_t packed = ((std::abs(l) - 1) << 1) | (l < 0 ? 1 : 0);
+            bool dup = false;
+            for (size_t r = start; r < lit.size(); ++r)
+                if (lit[r] == packed) { dup = true; break; }
+            if (!dup) lit.push_back(packed);
+        }
+        const int32_t len = (int32_t)(lit.size() - start);
+        if (len > kMaxClauseLen)
+            return fail(MSAT_EINVAL, "msat_create: clause " + std::to_string(j) + " has " +
+                                         std::to_string(len) + " literals (limit 1024)");
+        max_len = std::max(max_len, len);
+        coff[(size_t)j + 1] = (int32_t)lit.size();
+        wsum += weights ? weights[j] : 1;
+    }
+    const int64_t nnz = (int64_t)lit.size();
+    int32_t kfix = 0;
+    if (m > 0) {
+        kfix = coff[1] - coff[0];
+        for (int64_t j = 1; j < m && kfix > 0; ++j)
+            if (coff[(size_t)j + 1] - coff[(size_t)j] != kfix) kfix = 0;
+    }
+    // transposed CSR: occurrences of each variable in (clause, position) order
+    std::vector<int32_t> voff((size_t)n_vars + 1, 0);
+    for (int32_t L : lit) voff[(size_t)(L >> 1) + 1] += 1;
+    for (int32_t i = 0; i < n_vars; ++i) voff[(size_t)i + 1] += voff[(size_t)i];
+    std::vector<int32_t> occ((size_t)nnz);
+    {
+        std::vector<int32_t> fill(voff.begin(), voff.end() - 1);
+        for (int64_t j = 0; j < m; ++j)
+            for (int32_t p = coff[(size_t)j]; p < coff[(size_t)j + 1]; ++p) {
+                const int32_t L = lit[(size_t)p];
+                occ[(size_t)fill[(size_t)(L >> 1)]++] = (int32_t)(j << 1) | (L & 1);
+            }
+    }
+    int32_t max_deg = 0;
+    for (int32_t i = 0; i < n_vars; ++i) max_deg = std::max(max_deg, voff[(size_t)i + 1] - voff[(size_t)i]);
+    if ((int64_t)max_deg > 4095LL * 32 * kChunk)
+        return fail(MSAT_EINVAL, "msat_create: a variable occurs more than 4095*32768 times");
+    // variables whose occurrence sum is split into 1024-occurrence chunks
+    const int32_t heavy_deg = 64;
+    std::vector<int32_t> hvar, hchunk0(1, 0);
+    for (int32_t i = 0; i < n_vars; ++i) {
+        const int32_t d = voff[(size_t)i + 1] - voff[(size_t)i];
+        if (d > heavy_deg) {
+            hvar.push_back(i);
+            hchunk0.push_back(hchunk0.back() + (d + kChunk - 1) / kChunk);
+        }
+    }
+
+    msat_ctx *c = new (std::nothrow) msat_ctx();
+    if (!c) return fail(MSAT_ENOMEM, "msat_create: host allocation failed");
+    c->cfg = cfg;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->n = n_vars;
+    c->B = cfg.restarts;
+    c->m = m;
+    c->nnz = nnz;
+    c->kfix = kfix;
+    c->max_len = max_len;
+    c->max_deg = max_deg;
+    c->wsum = wsum;
+
+    const int32_t B = c->B;
+    const int64_t nB = (int64_t)n_vars * B;
+    const int VW = (B % 4 == 0) ? 4 : (B % 2 == 0 ? 2 : 1);
+    const int G = B / VW;
+    int rc = MSAT_OK;
+    int32_t *d_coff = nullptr, *d_lit = nullptr, *d_voff = nullptr, *d_occ = nullptr;
+    int32_t *d_hvar = nullptr, *d_hch = nullptr;
+    int64_t *d_w = nullptr;
+#define TRY_ALLOC(ptr, count)                          \
+    do {                                               \
+        rc = dalloc_t(c, &(ptr), (size_t)(count));     \
+        if (rc) { free_all(c); delete c; return rc; }  \
+    } while (0)
+    TRY_ALLOC(d_coff, m + 1);
+    TRY_ALLOC(d_lit, nnz);
+    if (weights) TRY_ALLOC(d_w, m);
+    TRY_ALLOC(d_voff, (int64_t)n_vars + 1);
+    TRY_ALLOC(d_occ, nnz);
+    TRY_ALLOC(d_hvar, (int64_t)hvar.size());
+    TRY_ALLOC(d_hch, (int64_t)hchunk0.size());
+    TRY_ALLOC(c->S.x, nB);
+    TRY_ALLOC(c->S.mom, nB);
+    TRY_ALLOC(c->S.vel, nB);
+    TRY_ALLOC(c->S.t0, nB);
+    TRY_ALLOC(c->S.t1, nB);
+    TRY_ALLOC(c->S.ubits, (m * B + 31) / 32 + 1);
+    TRY_ALLOC(c->S.bestx, nB);
+
+    DevInst &I = c->I;
+    I.n = n_vars;
+    I.m = (int32_t)m;
+    I.B = B;
+    I.kfix = kfix;
+    I.coff = d_coff;
+    I.lit = d_lit;
+    I.w = d_w;
+    I.voff = d_voff;
+    I.occ = d_occ;
+    I.heavy_deg = heavy_deg;
+    I.n_heavy = (int32_t)hvar.size();
+    I.heavy_chunks = hchunk0.back();
+    I.heavy_var = d_hvar;
+    I.heavy_chunk0 = d_hch;
+
+    DevStep &D = c->D;
+    D.fwd_blocks = fwd_grid_blocks(I);
+    TRY_ALLOC(D.sc, 1);
+    TRY_ALLOC(D.wu_acc, B);
+    TRY_ALLOC(D.cost, B);
+    TRY_ALLOC(D.best, B);
+    TRY_ALLOC(D.improved, B);
+    TRY_ALLOC(D.cscale, B);
+    TRY_ALLOC(D.loss, B);
+    TRY_ALLOC(D.lpart, (int64_t)D.fwd_blocks * B);
+    TRY_ALLOC(D.hpart, std::max<int64_t>(1, I.heavy_chunks) * B);
+    TRY_ALLOC(D.hcount, std::max<int64_t>(1, (int64_t)hvar.size() * G));
+#undef TRY_ALLOC
+
+    cudaStream_t st = c->stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    StepScalars sc{};
+    sc.counter = 0;
+    sc.steps_done = 0;
+    sc.p1 = 1.0;
+    sc.p2 = 1.0;
+    sc.lr = cfg.lr;
+    sc.beta1 = cfg.beta1;
+    sc.beta2 = cfg.beta2;
+    sc.eps = cfg.eps;
+    sc.b1f = (float)cfg.beta1;
+    sc.b2f = (float)cfg.beta2;
+    sc.omb1f = (float)(1.0 - cfg.beta1);
+    sc.omb2f = (float)(1.0 - cfg.beta2);
+    sc.epsf = (float)cfg.eps;
+    std::vector<long long> best((size_t)B, (long long)wsum);
+    cudaError_t e = cudaSuccess;
+    if (!e) e = up(d_coff, coff.data(), sizeof(int32_t) * coff.size());
+    if (!e) e = up(d_lit, lit.data(), sizeof(int32_t) * lit.size());
+    if (!e && weights) e = up(d_w, weights, sizeof(int64_t) * (size_t)m);
+    if (!e) e = up(d_voff, voff.data(), sizeof(int32_t) * voff.size());
+    if (!e) e = up(d_occ, occ.data(), sizeof(int32_t) * occ.size());
+    if (!e) e = up(d_hvar, hvar.data(), sizeof(int32_t) * hvar.size());
+    if (!e) e = up(d_hch, hchunk0.data(), sizeof(int32_t) * hchunk0.size());
+    if (!e) e = up(D.sc, &sc, sizeof(sc));
+    if (!e) e = up(D.best, best.data(), sizeof(long long) * best.size());
+    if (!e) e = cudaMemsetAsync(D.wu_acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (!e) e = cudaMemsetAsync(D.improved, 0, sizeof(int) * (size_t)B, st);
+    if (!e) e = cudaMemsetAsync(D.cost, 0, sizeof(long long) * (size_t)B, st);
+    if (!e) e = cudaMemsetAsync(D.loss, 0, sizeof(float) * (size_t)B, st);
+    if (!e) e = cudaMemsetAsync(D.hcount, 0, sizeof(unsigned) * std::max<size_t>(1, hvar.size() * (size_t)G), st);
+    if (!e) e = cudaMemsetAsync(c->S.ubits, 0, sizeof(uint32_t) * (size_t)((m * B + 31) / 32 + 1), st);
+    if (!e) e = launch_init(I, c->S, cfg.seed_x, st);
+    if (!e) e = cudaStreamSynchronize(st);  // host vectors above are freed on return
+    if (e) {
+        rc = cuda_fail(e, "msat_create: upload / init");
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return MSAT_OK;
+}
+
+extern "C" void msat_destroy(msat_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+extern "C" int msat_set_stream(msat_ctx *c, void *stream) {
+    if (!c) return fail(MSAT_EINVAL, "msat_set_stream: ctx is NULL");
+    c->stream = (cudaStream_t)stream;
+    return MSAT_OK;
+}
+
+// One evaluation of the current x (final evaluation of a msat_step call).
+static cudaError_t eval_current(msat_ctx *c) {
+    cudaError_t e = launch_forward(c->I, c->S, c->D, FWD_EVAL, nullptr, c->stream);
+    if (e) return e;
+    return launch_backward(c->I, c->S, c->D, BWD_BITS_ONLY, nullptr, nullptr, nullptr, nullptr,
+                           c->stream);
+}
+
+extern "C" int msat_step(msat_ctx *c, int32_t n_steps, float *loss_out, int64_t *cost_out) {
+    if (!c) return fail(MSAT_EINVAL, "msat_step: ctx is NULL");
+    if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
+    cudaError_t e = cudaSuccess;
+    for (int32_t s = 0; s < n_steps && !e; ++s) {
+        e = launch_forward(c->I, c->S, c->D, FWD_STEP, nullptr, c->stream);
+        if (!e)
+            e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, nullptr,
+                                c->stream);
+    }
+    if (!e) e = eval_current(c);
+    if (e) return cuda_fail(e, "msat_step: kernel launch");
+    c->steps_done_host += n_steps;
+    if (loss_out)
+        MSAT_CUDA_TRY(cudaMemcpyAsync(loss_out, c->D.loss, sizeof(float) * (size_t)c->B,
+                                      cudaMemcpyDeviceToHost, c->stream));
+    if (cost_out)
+        MSAT_CUDA_TRY(cudaMemcpyAsync(cost_out, c->D.cost, sizeof(int64_t) * (size_t)c->B,
+                                      cudaMemcpyDeviceToHost, c->stream));
+    if (loss_out || cost_out) MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return MSAT_OK;
+}
+
+extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
+                             int32_t backend) {
+    if (!c) return fail(MSAT_EINVAL, "msat_evaluate: ctx is NULL");
+    if (nb < 1 || !assign_pm1 || !cost_out)
+        return fail(MSAT_EINVAL, "msat_evaluate: need nb >= 1 and non-NULL buffers");
+    if (backend == MSAT_BACKEND_SPARSE) {
+        cudaError_t e = launch_eval_sparse(c->I, assign_pm1, nb, (long long *)cost_out, c->stream);
+        if (e) return cuda_fail(e, "msat_evaluate: sparse kernel");
+        return MSAT_OK;
+    }
+    if (backend == MSAT_BACKEND_DENSE)
+        return fail(MSAT_EINVAL, "msat_evaluate: the dense backend is not available in this build");
+    return fail(MSAT_EINVAL, "msat_evaluate: unknown backend");
+}
+
+extern "C" int msat_best(msat_ctx *c, uint8_t *assign01, int64_t *best_cost) {
+    if (!c) return fail(MSAT_EINVAL, "msat_best: ctx is NULL");
+    if (best_cost)
+        MSAT_CUDA_TRY(cudaMemcpyAsync(best_cost, c->D.best, sizeof(int64_t) * (size_t)c->B,
+                                      cudaMemcpyDeviceToHost, c->stream));
+    std::vector<uint8_t> tmp;
+    if (assign01) {
+        tmp.resize((size_t)c->n * c->B);
+        MSAT_CUDA_TRY(cudaMemcpyAsync(tmp.data(), c->S.bestx, tmp.size(), cudaMemcpyDeviceToHost,
+                                      c->stream));
+    }
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (assign01)
+        for (int32_t i = 0; i < c->n; ++i)
+            for (int32_t b = 0; b < c->B; ++b)
+                assign01[(size_t)b * c->n + i] = tmp[(size_t)i * c->B + b];
+    return MSAT_OK;
+}
+
+extern "C" int msat_get_x(msat_ctx *c, float *x_host) {
+    if (!c || !x_host) return fail(MSAT_EINVAL, "msat_get_x: NULL argument");
+    MSAT_CUDA_TRY(cudaMemcpyAsync(x_host, c->S.x, sizeof(float) * (size_t)c->n * c->B,
+                                  cudaMemcpyDeviceToHost, c->stream));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return MSAT_OK;
+}
+
+extern "C" int msat_get_info(msat_ctx *c, msat_info *info) {
+    if (!c || !info) return fail(MSAT_EINVAL, "msat_get_info: NULL argument");
+    StepScalars sc;
+    MSAT_CUDA_TRY(cudaMemcpyAsync(&sc, c->D.sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    memset(info, 0, sizeof(*info));
+    info->n = c->n;
+    info->restarts = c->B;
+    info->m = c->m;
+    info->nnz = c->nnz;
+    info->steps_done = sc.steps_done;
+    info->device_bytes = c->device_bytes;
+    info->max_clause_len = c->max_len;
+    info->max_degree = c->max_deg;
+    info->n_heavy = c->I.n_heavy;
+    info->uniform_len = c->kfix;
+    return MSAT_OK;
+}
+
+extern "C" int msat_get_state(msat_ctx *c, float *x, float *mom, float *vel, int64_t *best_cost,
+                              uint8_t *best_assign, int64_t *steps_done, double *adam_pow) {
+    if (!c) return fail(MSAT_EINVAL, "msat_get_state: ctx is NULL");
+    const size_t nB = (size_t)c->n * c->B;
+    cudaStream_t st = c->stream;
+    if (x) MSAT_CUDA_TRY(cudaMemcpyAsync(x, c->S.x, sizeof(float) * nB, cudaMemcpyDeviceToHost, st));
+    if (mom) MSAT_CUDA_TRY(cudaMemcpyAsync(mom, c->S.mom, sizeof(float) * nB, cudaMemcpyDeviceToHost, st));
+    if (vel) MSAT_CUDA_TRY(cudaMemcpyAsync(vel, c->S.vel, sizeof(float) * nB, cudaMemcpyDeviceToHost, st));
+    if (best_cost)
+        MSAT_CUDA_TRY(cudaMemcpyAsync(best_cost, c->D.best, sizeof(int64_t) * (size_t)c->B,
+                                      cudaMemcpyDeviceToHost, st));
+    if (best_assign)
+        MSAT_CUDA_TRY(cudaMemcpyAsync(best_assign, c->S.bestx, nB, cudaMemcpyDeviceToHost, st));
+    StepScalars sc;
+    MSAT_CUDA_TRY(cudaMemcpyAsync(&sc, c->D.sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (steps_done) *steps_done = sc.steps_done;
+    if (adam_pow) {
+        adam_pow[0] = sc.p1;
+        adam_pow[1] = sc.p2;
+    }
+    return MSAT_OK;
+}
+
+extern "C" int msat_set_state(msat_ctx *c, const float *x, const float *mom, const float *vel,
+                              const int64_t *best_cost, const uint8_t *best_assign,
+                              int64_t steps_done, const double *adam_pow) {
+    if (!c || !x || !mom || !vel || !best_cost || !best_assign || !adam_pow)
+        return fail(MSAT_EINVAL, "msat_set_state: NULL argument");
+    if (steps_done < 0) return fail(MSAT_EINVAL, "msat_set_state: steps_done < 0");
+    const size_t nB = (size_t)c->n * c->B;
+    cudaStream_t st = c->stream;
+    StepScalars sc;
+    MSAT_CUDA_TRY(cudaMemcpyAsync(&sc, c->D.sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(st));
+    sc.counter = 0;
+    sc.steps_done = steps_done;
+    sc.p1 = adam_pow[0];
+    sc.p2 = adam_pow[1];
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->D.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.x, x, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.mom, mom, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.vel, vel, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->D.best, best_cost, sizeof(int64_t) * (size_t)c->B,
+                                  cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.bestx, best_assign, nB, cudaMemcpyHostToDevice, st));
+    // the forward pass reads tanh(x) from the buffer of the current parity
+    float *tcur = (steps_done & 1) ? c->S.t1 : c->S.t0;
+    cudaError_t e = launch_tanh(c->S.x, tcur, (int64_t)nB, st);
+    if (e) return cuda_fail(e, "msat_set_state: tanh kernel");
+    MSAT_CUDA_TRY(cudaStreamSynchronize(st));
+    c->steps_done_host = steps_done;
+    return MSAT_OK;
+}
+
+// ------------------------------------------------------------ probe path
+
+static int ensure_probe(msat_ctx *c) {
+    if (c->probe_ready) return MSAT_OK;
+    const int32_t B = c->B;
+    const int64_t nB = (int64_t)c->n * B;
+    c->PS = c->S;
+    c->PD = c->D;
+    int rc;
+    if ((rc = dalloc_t(c, &c->PS.t0, nB))) return rc;
+    c->PS.t1 = c->PS.t0;
+    if ((rc = dalloc_t(c, &c->PS.ubits, (c->m * B + 31) / 32 + 1))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.sc, 1))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.wu_acc, B))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.cost, B))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.cscale, B))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.lpart, (int64_t)c->PD.fwd_blocks * B))) return rc;
+    c->PD.best = nullptr;
+    c->PD.improved = nullptr;
+    StepScalars sc;
+    MSAT_CUDA_TRY(cudaMemcpyAsync(&sc, c->D.sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    sc.counter = 0;
+    sc.steps_done = 0;
+    MSAT_CUDA_TRY(cudaMemcpyAsync(c->PD.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
+    MSAT_CUDA_TRY(cudaMemsetAsync(c->PD.wu_acc, 0, sizeof(unsigned long long) * (size_t)B, c->stream));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->probe_ready = true;
+    return MSAT_OK;
+}
+
+extern "C" int msat_forward(msat_ctx *c, const float *x, float *loss, int64_t *cost) {
+    if (!c || !x || !loss) return fail(MSAT_EINVAL, "msat_forward: NULL argument");
+    int rc = ensure_probe(c);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    const int64_t nB = (int64_t)c->n * c->B;
+    cudaError_t e = launch_tanh(x, c->PS.t0, nB, st);
+    if (!e) e = launch_forward(c->I, c->PS, c->PD, FWD_PROBE, c->PS.t0, st);
+    DevStep d = c->PD;
+    d.loss = loss;
+    if (!e) e = launch_loss_reduce(d, c->B, st);
+    if (!e && cost)
+        e = cudaMemcpyAsync(cost, c->PD.cost, sizeof(int64_t) * (size_t)c->B,
+                            cudaMemcpyDeviceToDevice, st);
+    if (e) return cuda_fail(e, "msat_forward");
+    return MSAT_OK;
+}
+
+extern "C" int msat_backward(msat_ctx *c, const float *gscale, float *grad) {
+    if (!c || !grad) return fail(MSAT_EINVAL, "msat_backward: NULL argument");
+    if (!c->probe_ready) return fail(MSAT_ESTATE, "msat_backward: no msat_forward before it");
+    // 1 - t^2 comes from the tanh(x) stored by msat_forward
+    cudaError_t e = launch_backward(c->I, c->PS, c->PD, BWD_GRAD_ONLY, nullptr, c->PS.t0, gscale,
+                                    grad, c->stream);
+    if (e) return cuda_fail(e, "msat_backward");
+    return MSAT_OK;
+}

@@ -1,0 +1,189 @@
+// Internal declarations of the GB300 MaxSAT engine: device views of the
+// instance and the step state, the fixed-order fp32 arithmetic shared by the
+// kernels, and the launchers each kernel file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/msat.h"
+
+namespace msat {
+
+// ------------------------------------------------------------ error plumbing
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MSAT_CUDA_TRY(expr)                                  \
+    do {                                                     \
+        cudaError_t e__ = (expr);                            \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------- device views
+
+// Clause CSR and its transpose (variable -> occurrences), both in stored
+// literal order.  lit = var << 1 | neg; occ = clause << 1 | neg.
+struct DevInst {
+    int32_t n;
+    int32_t m;
+    int32_t B;
+    int32_t kfix;                 // common clause length (> 0) or 0
+    const int32_t *coff;          // [m+1] (unused when kfix > 0)
+    const int32_t *lit;           // [nnz]
+    const int64_t *w;             // [m] or nullptr (all weights 1)
+    const int32_t *voff;          // [n+1]
+    const int32_t *occ;           // [nnz]
+    int32_t heavy_deg;            // degree above which a variable is split
+    int32_t n_heavy;              // number of heavy variables
+    long long heavy_chunks;       // total chunks of the heavy variables
+    const int32_t *heavy_var;     // [n_heavy] variable ids
+    const int32_t *heavy_chunk0;  // [n_heavy+1] prefix of chunk counts
+};
+
+// Scalars of the optimizer step shared by all restarts.
+struct StepScalars {
+    unsigned int counter;   // finished-block counter of the forward kernel
+    unsigned int pad0;
+    long long steps_done;   // Adam steps taken
+    double p1, p2;          // beta1^steps_done, beta2^steps_done (running products)
+    float a_t, r_t;         // lr / (1 - p1), 1 / sqrt(1 - p2) of the step in flight
+    double lr, beta1, beta2, eps;
+    float b1f, b2f, omb1f, omb2f, epsf;
+    float pad1;
+};
+
+// Per-restart step state plus scratch.
+struct DevStep {
+    StepScalars *sc;
+    unsigned long long *wu_acc;  // [B] atomic accumulator of sum_U w
+    long long *cost;             // [B] cost of the evaluated x
+    long long *best;             // [B] best cost so far
+    int *improved;               // [B] cost < best at the last evaluation
+    float *cscale;               // [B] 2 / (float)W_U (0 if W_U = 0)
+    float *loss;                 // [B] loss of the last updated x
+    float *lpart;                // [fwd_blocks][B] per-block loss partials
+    int fwd_blocks;              // blocks of the forward launch
+    float *hpart;                // [total heavy chunks][B] heavy chunk partials
+    unsigned int *hcount;        // [n_heavy][G] heavy finish counters
+};
+
+struct DevState {
+    float *x, *mom, *vel;  // [n][B]
+    float *t0, *t1;        // double-buffered tanh(x), [n][B]
+    uint32_t *ubits;       // unsat bits, flat index j*B + b
+    uint8_t *bestx;        // [n][B] best assignment (0/1)
+};
+
+// Kernel modes of the variable pass.
+enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
+
+constexpr int kThreads = 256;
+constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
+constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
+
+// ------------------------------------------------------- fp32 arithmetic
+// Fixed-order float arithmetic of the step.  Every operation is a single
+// IEEE operation rounded to nearest; fused multiply-adds appear only where
+// written as fmaf (the library is built with -fmad=false).
+
+// e^y - 1 for 0 <= y <= 18: y = k ln2 + r (Cody-Waite split of ln2 with a
+// 16-bit-exact high part), e^r - 1 = r + r^2 q(r), q the Taylor series of
+// (e^r - 1 - r) / r^2 to degree 6 (terms 1/2! .. 1/8!), Horner with fmaf;
+// e^y - 1 = 2^k (e^r - 1) + (2^k - 1).
+__device__ __forceinline__ float expm1_fixed(float y) {
+    const float kInvLn2 = 1.44269504088896341f;
+    const float kLn2Hi = 0.693145751953125f;
+    const float kLn2Lo = 1.428606820309417232e-06f;
+    float kf = rintf(y * kInvLn2);
+    float r = fmaf(-kf, kLn2Hi, y);
+    r = fmaf(-kf, kLn2Lo, r);
+    float q = 1.0f / 40320.0f;
+    q = fmaf(q, r, 1.0f / 5040.0f);
+    q = fmaf(q, r, 1.0f / 720.0f);
+    q = fmaf(q, r, 1.0f / 120.0f);
+    q = fmaf(q, r, 1.0f / 24.0f);
+    q = fmaf(q, r, 1.0f / 6.0f);
+    q = fmaf(q, r, 0.5f);
+    float rr = r * r;
+    float em = fmaf(rr, q, r);
+    int k = (int)kf;
+    if (k == 0) return em;
+    float scale = __int_as_float((127 + k) << 23);
+    return fmaf(scale, em, scale - 1.0f);
+}
+
+// tanh(a) = sign(a) * em1 / (em1 + 2), em1 = e^{2|a|} - 1; 1 for |a| >= 9.
+// tanh(a) > 0 exactly when a > 0.
+__device__ __forceinline__ float tanh_fixed(float a) {
+    float s = fabsf(a);
+    float r;
+    if (!(s < 9.0f)) {
+        r = (s != s) ? s : 1.0f;
+    } else {
+        float em1 = expm1_fixed(s + s);
+        r = em1 / (em1 + 2.0f);
+    }
+    return copysignf(r, a);
+}
+
+// Leaf counter of the fixed summation order: 32-term leaves are summed in
+// order by the caller; finished leaves are pushed here and merged into
+// dyadic blocks (binary counter), and finish() combines what is left from
+// the smallest (rightmost) block to the largest.  LEVELS bounds the leaf
+// count to 2^LEVELS - 1.
+template <int LEVELS>
+struct LeafCounter {
+    float blk[LEVELS];
+    unsigned cnt;
+    __device__ __forceinline__ void init() { cnt = 0; }
+    __device__ __forceinline__ void push(float v) {
+        bool carry = true;
+#pragma unroll
+        for (int p = 0; p < LEVELS; ++p) {
+            if (carry) {
+                if (cnt & (1u << p)) {
+                    v = blk[p] + v;
+                } else {
+                    blk[p] = v;
+                    carry = false;
+                }
+            }
+        }
+        ++cnt;
+    }
+    __device__ __forceinline__ float finish() const {
+        float r = 0.0f;
+        bool have = false;
+#pragma unroll
+        for (int p = 0; p < LEVELS; ++p) {
+            if (cnt & (1u << p)) {
+                r = have ? (blk[p] + r) : blk[p];
+                have = true;
+            }
+        }
+        return r;
+    }
+};
+
+// ----------------------------------------------------------------- launchers
+// Implemented in k_step.cu / k_eval.cu; each returns a cudaError_t.
+
+cudaError_t launch_init(const DevInst &I, const DevState &S, uint64_t seed, cudaStream_t st);
+int fwd_grid_blocks(const DevInst &I);
+enum { FWD_STEP = 0, FWD_EVAL = 1, FWD_PROBE = 2 };
+cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
+                           const float *t_override, cudaStream_t st);
+cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
+                            const float *x_override, const float *t_override,
+                            const float *gscale, float *grad_out, cudaStream_t st);
+cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st);
+cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
+cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
+                               cudaStream_t st);
+
+}  // namespace msat

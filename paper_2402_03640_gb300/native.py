@@ -1,0 +1,102 @@
+"""ctypes view of libmsat.so (the C ABI declared in include/msat.h).
+
+Argument marshalling only: every step of the solving loop runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MSAT_OK = 0
+MSAT_EINVAL = -1
+MSAT_ENOMEM = -2
+MSAT_EBUDGET = -3
+MSAT_ETIMEOUT = -4
+MSAT_ECUDA = -5
+MSAT_EAGAIN = -6
+MSAT_ESTATE = -7
+
+BACKEND_SPARSE = 0
+BACKEND_DENSE = 1
+
+_ERRNAMES = {MSAT_EINVAL: "EINVAL", MSAT_ENOMEM: "ENOMEM", MSAT_EBUDGET: "EBUDGET",
+             MSAT_ETIMEOUT: "ETIMEOUT", MSAT_ECUDA: "ECUDA", MSAT_EAGAIN: "EAGAIN",
+             MSAT_ESTATE: "ESTATE"}
+
+
+class MsatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"msat {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class msat_config(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("restarts", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("seed_x", ctypes.c_uint64)]
+
+
+class msat_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("restarts", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("steps_done", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("max_clause_len", ctypes.c_int32),
+                ("max_degree", ctypes.c_int32), ("n_heavy", ctypes.c_int32),
+                ("uniform_len", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO_PATH
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libmsat.so.  Raises if it is missing (build it with build.py or
+    __graft_entry__.build()); build_if_missing compiles it first."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.SO_PATH
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is not built; run paper_2402_03640_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "msat_config_default": ([P], ctypes.c_int),
+            "msat_create": ([P, i32, i64, P, P, P, P, P], ctypes.c_int),
+            "msat_destroy": ([P], None),
+            "msat_set_stream": ([P, P], ctypes.c_int),
+            "msat_step": ([P, i32, P, P], ctypes.c_int),
+            "msat_evaluate": ([P, P, i32, P, i32], ctypes.c_int),
+            "msat_best": ([P, P, P], ctypes.c_int),
+            "msat_get_x": ([P, P], ctypes.c_int),
+            "msat_forward": ([P, P, P, P], ctypes.c_int),
+            "msat_backward": ([P, P, P], ctypes.c_int),
+            "msat_get_info": ([P, P], ctypes.c_int),
+            "msat_get_state": ([P, P, P, P, P, P, P, P], ctypes.c_int),
+            "msat_set_state": ([P, P, P, P, P, P, i64, P], ctypes.c_int),
+            "msat_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def check(rc: int) -> None:
+    if rc != MSAT_OK:
+        msg = load().msat_last_error()
+        raise MsatError(rc, msg.decode() if msg else "")

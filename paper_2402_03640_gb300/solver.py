@@ -1,0 +1,211 @@
+"""Python face of the GB300 MaxSAT gradient engine.
+
+Solver wraps one msat_ctx (Algorithm 1 of arXiv 2402.03640 on the GPU with B
+restarts); MsatLoss exposes the relaxed objective of Sec. 4 as a
+torch.autograd.Function whose forward and backward are the library's
+kernels.  Host arrays are numpy; device arrays are torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import native
+from .native import check
+
+
+def _p(a) -> Optional[ctypes.c_void_p]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Solver:
+    """One CNF instance with B restarts resident on the GPU.
+
+    n, off, lits, weights follow include/msat.h (DIMACS literals, int64
+    offsets, optional int64 weights >= 1).  stream: a torch.cuda.Stream, a
+    raw cudaStream_t integer, or None for torch's current stream.
+    """
+
+    def __init__(self, n: int, off, lits, weights=None, restarts: int = 1, seed_x: int = 1,
+                 lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 stream=None):
+        lib = native.load()
+        self._lib = lib
+        cfg = native.msat_config()
+        check(lib.msat_config_default(ctypes.byref(cfg)))
+        cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
+        cfg.restarts = int(restarts)
+        cfg.seed_x = int(seed_x)
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        lits = np.ascontiguousarray(lits, dtype=np.int32)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)
+        self.n = int(n)
+        self.m = int(off.shape[0] - 1)
+        self.B = int(restarts)
+        self._ctx = ctypes.c_void_p()
+        st = _stream_handle(stream)
+        check(lib.msat_create(ctypes.byref(self._ctx), self.n, self.m, _p(off), _p(lits), _p(w),
+                              ctypes.byref(cfg), ctypes.c_void_p(st) if st else None))
+
+    @classmethod
+    def from_cnf(cls, cnf, **kw) -> "Solver":
+        return cls(cnf.n, cnf.off, cnf.lits, cnf.weights, **kw)
+
+    # -------------------------------------------------------------- life
+    def close(self) -> None:
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.msat_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream) -> None:
+        st = _stream_handle(stream)
+        check(self._lib.msat_set_stream(self._ctx, ctypes.c_void_p(st) if st else None))
+
+    # -------------------------------------------------------------- loop
+    def step(self, n_steps: int, want_loss: bool = True, want_cost: bool = True
+             ) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
+        """n_steps iterations of Algorithm 1 plus a final evaluation; returns
+        (loss at the last updated x, cost of the final x), each [B] or None."""
+        loss = np.empty(self.B, np.float32) if want_loss else None
+        cost = np.empty(self.B, np.int64) if want_cost else None
+        check(self._lib.msat_step(self._ctx, int(n_steps), _p(loss), _p(cost)))
+        return loss, cost
+
+    def step_async(self, n_steps: int) -> None:
+        check(self._lib.msat_step(self._ctx, int(n_steps), None, None))
+
+    def best(self) -> Tuple[np.ndarray, np.ndarray]:
+        a = np.empty((self.B, self.n), np.uint8)
+        c = np.empty(self.B, np.int64)
+        check(self._lib.msat_best(self._ctx, _p(a), _p(c)))
+        return a, c
+
+    def x(self) -> np.ndarray:
+        out = np.empty((self.n, self.B), np.float32)
+        check(self._lib.msat_get_x(self._ctx, _p(out)))
+        return out
+
+    def info(self) -> dict:
+        inf = native.msat_info()
+        check(self._lib.msat_get_info(self._ctx, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def get_state(self) -> dict:
+        nB = (self.n, self.B)
+        st = dict(x=np.empty(nB, np.float32), mom=np.empty(nB, np.float32),
+                  vel=np.empty(nB, np.float32), best_cost=np.empty(self.B, np.int64),
+                  best_assign=np.empty(nB, np.uint8), steps_done=np.zeros(1, np.int64),
+                  adam_pow=np.zeros(2, np.float64))
+        check(self._lib.msat_get_state(self._ctx, _p(st["x"]), _p(st["mom"]), _p(st["vel"]),
+                                       _p(st["best_cost"]), _p(st["best_assign"]),
+                                       _p(st["steps_done"]), _p(st["adam_pow"])))
+        return st
+
+    def set_state(self, st: dict) -> None:
+        arr = {k: np.ascontiguousarray(v) for k, v in st.items()}
+        check(self._lib.msat_set_state(self._ctx, _p(arr["x"].astype(np.float32, copy=False)),
+                                       _p(arr["mom"].astype(np.float32, copy=False)),
+                                       _p(arr["vel"].astype(np.float32, copy=False)),
+                                       _p(arr["best_cost"].astype(np.int64, copy=False)),
+                                       _p(arr["best_assign"].astype(np.uint8, copy=False)),
+                                       int(arr["steps_done"].reshape(-1)[0]),
+                                       _p(arr["adam_pow"].astype(np.float64, copy=False))))
+
+    # -------------------------------------------------------- evaluation
+    def evaluate(self, assign_pm1, backend: str = "sparse"):
+        """Exact cost of a batch of +-1 assignments (torch int8 CUDA [n][nb]);
+        returns a torch int64 CUDA tensor [nb]."""
+        import torch
+        a = assign_pm1
+        if a.dtype != torch.int8 or not a.is_cuda or a.dim() != 2 or a.shape[0] != self.n:
+            raise ValueError("assign_pm1 must be a CUDA int8 tensor of shape [n, nb]")
+        a = a.contiguous()
+        nb = int(a.shape[1])
+        out = torch.empty(nb, dtype=torch.int64, device=a.device)
+        be = {"sparse": native.BACKEND_SPARSE, "dense": native.BACKEND_DENSE}[backend]
+        check(self._lib.msat_evaluate(self._ctx, _p(a), nb, _p(out), be))
+        return out
+
+    # ---------------------------------------------------- differentiable
+    def forward(self, x):
+        import torch
+        x = x.contiguous()
+        if x.dtype != torch.float32 or not x.is_cuda or tuple(x.shape) != (self.n, self.B):
+            raise ValueError("x must be a CUDA float32 tensor of shape [n, B]")
+        loss = torch.empty(self.B, dtype=torch.float32, device=x.device)
+        cost = torch.empty(self.B, dtype=torch.int64, device=x.device)
+        check(self._lib.msat_forward(self._ctx, _p(x), _p(loss), _p(cost)))
+        return loss, cost
+
+    def backward(self, gscale=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        grad = torch.empty((self.n, self.B), dtype=torch.float32, device=dev)
+        g = None if gscale is None else gscale.contiguous().to(torch.float32)
+        check(self._lib.msat_backward(self._ctx, _p(g), _p(grad)))
+        return grad
+
+
+def _make_autograd():
+    import torch
+
+    class MsatLoss(torch.autograd.Function):
+        """loss[b] = sum_{unsat j} w_j f_j^2 / sum_{unsat j} w_j for restart b,
+        f = tanh(x) . W (Sec. 4); backward through the library's variable-pass
+        kernel (the unsat mask is treated as a constant)."""
+
+        @staticmethod
+        def forward(ctx, x, solver):
+            loss, _ = solver.forward(x)
+            ctx.solver = solver
+            return loss
+
+        @staticmethod
+        def backward(ctx, gout):
+            grad = ctx.solver.backward(gout)
+            return grad, None
+
+    return MsatLoss
+
+
+_MsatLoss = None
+
+
+def msat_loss(x, solver: Solver):
+    """Differentiable relaxed objective: MsatLoss.apply(x, solver)."""
+    global _MsatLoss
+    if _MsatLoss is None:
+        _MsatLoss = _make_autograd()
+    return _MsatLoss.apply(x, solver)

@@ -1,0 +1,242 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+Unsat counts, weighted costs, rounded (best) assignments and relaxed x are
+compared bit for bit with the oracle's FP32-canon mode (same seeds, same
+instances); losses and gradients within 1e-5 relative of the FP64 mode.
+Sizes span several thread blocks with ragged tails; the full-size
+configurations are checked on short trajectories."""
+import numpy as np
+import pytest
+
+from synth import Cnf, pigeonhole, planted_ksat, uniform_ksat, zipf_weighted
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2402_03640_gb300 as p
+    from paper_2402_03640_gb300 import build
+    build.build()
+    p.load()
+    return p
+
+
+def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1):
+    """Cost after each evaluation (x_0 .. x_steps), loss of each update, final x."""
+    costs, losses = [], []
+    with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=seed_x, lr=lr) as s:
+        costs.append(s.step(0, want_loss=False)[1])
+        done = 0
+        while done < steps:
+            k = min(chunk, steps - done)
+            loss, cost = s.step(k)
+            done += k
+            costs.append(cost)
+            losses.append(loss)
+        x = s.x()
+        assign, best = s.best()
+        info = s.info()
+    return dict(cost_hist=np.array(costs), loss_hist=np.array(losses), x=x, best_assign=assign,
+                best_cost=best, info=info)
+
+
+def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, loss_every=1):
+    ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr)
+    got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk)
+    idx = [0] + [min(k, steps) for k in range(chunk, steps + chunk, chunk)] if steps else [0]
+    want_costs = ref["cost_hist"][idx]
+    assert np.array_equal(got["cost_hist"], want_costs), "unsat cost history differs"
+    assert np.array_equal(got["x"].astype(np.float64), ref["x_final"]), "relaxed x differs"
+    assert np.array_equal(got["best_cost"], ref["best_cost"])
+    assert np.array_equal(got["best_assign"], ref["best_assign"])
+    if chunk == 1 and steps:
+        # loss of x_s vs the oracle's (reported in double from the same float f)
+        assert np.allclose(got["loss_hist"], ref["loss_hist"], rtol=1e-5, atol=1e-7)
+    return got, ref
+
+
+_PKG = {}
+
+
+def pkg_module():
+    return _PKG["p"]
+
+
+@pytest.fixture(autouse=True)
+def _remember(pkg):
+    _PKG["p"] = pkg
+
+
+# ---------------------------------------------------------------- init
+
+@pytest.mark.parametrize("n,B", [(50, 1), (1000, 16), (777, 8), (5000, 256), (33, 2)])
+def test_init_matches_oracle(pkg, oracle, n, B):
+    cnf = uniform_ksat(max(n, 3), 4 * n, 3, seed=0)
+    with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1) as s:
+        x = s.x()
+    assert np.array_equal(x, oracle.init_x(cnf.n, B, 1))
+
+
+# --------------------------------------------------------- trajectories
+
+def test_config0_full_trajectory(pkg, oracle):
+    """Uniform 3-SAT n=50, m=215 (seed 0), x from seed 1, 1000 Adam steps
+    at lr 1e-4: every unsat count, the final x and the best assignment."""
+    cnf = uniform_ksat(50, 215, 3, seed=0)
+    got, ref = check_bit_exact(oracle, cnf, 1, 1000, 1e-4, chunk=1)
+    assert got["cost_hist"][-1, 0] == ref["cost_hist"][-1, 0]
+
+
+@pytest.mark.parametrize("B", [1, 2, 4, 16, 64])
+def test_restarts_trajectory(pkg, oracle, B):
+    cnf = uniform_ksat(300, 1290, 3, seed=5)
+    check_bit_exact(oracle, cnf, B, 60, 1e-2)
+
+
+def test_larger_lr_chunked_steps(pkg, oracle):
+    cnf = uniform_ksat(1000, 4300, 3, seed=2)
+    check_bit_exact(oracle, cnf, 4, 40, 3e-2, chunk=7)
+
+
+def test_weighted_zipf_with_heavy_variables(pkg, oracle):
+    cnf = zipf_weighted(3000, 20000, seed=1)
+    deg = np.bincount(np.abs(cnf.lits) - 1, minlength=cnf.n)
+    assert deg.max() > 2048                      # several 1024-occurrence chunks
+    got, _ = check_bit_exact(oracle, cnf, 1, 25, 1e-2)
+    assert got["info"]["n_heavy"] > 0
+    check_bit_exact(oracle, cnf, 4, 10, 1e-2)
+
+
+def test_long_clauses_and_mixed_lengths(pkg, oracle):
+    cnf = pigeonhole(40)                         # 40-literal pigeon clauses
+    assert np.diff(cnf.off).max() == 40
+    check_bit_exact(oracle, cnf, 2, 15, 5e-2)
+
+
+def test_planted_instance_reaches_zero_and_freezes(pkg, oracle):
+    cnf = planted_ksat(40, 120, 3, seed=1)
+    got, ref = check_bit_exact(oracle, cnf, 4, 400, 5e-2)
+    assert (got["best_cost"] == 0).any()
+
+
+def test_degenerate_clauses(pkg, oracle):
+    cnf = Cnf.from_clauses(6, [[1, 1, 2], [-3, 3], [], [4, -5, 6, -4], [2], [-2], [5, 6, 1, 2]],
+                           weights=[3, 1, 7, 2, 5, 5, 1])
+    check_bit_exact(oracle, cnf, 2, 50, 5e-2)
+    empty = Cnf(n=5, off=np.zeros(1, np.int64), lits=np.zeros(0, np.int32))
+    got = gpu_trajectory(pkg, empty, 1, 3, 1e-2)
+    assert got["cost_hist"].max() == 0
+
+
+# --------------------------------------------------------- full sizes
+
+def test_config1_batched_restarts(pkg, oracle):
+    """Uniform 3-SAT n=5000, m=21500, B=256 restarts: 3 steps bit for bit."""
+    cnf = uniform_ksat(5000, 21500, 3, seed=0)
+    check_bit_exact(oracle, cnf, 256, 3, 1e-4)
+
+
+def test_config2_weighted_zipf_full(pkg, oracle):
+    """n=200000, m=1000000, Zipf(1.2), weights 1..1000, B=1: 6 steps."""
+    cnf = zipf_weighted(200000, 1000000, seed=0)
+    check_bit_exact(oracle, cnf, 1, 6, 1e-4)
+
+
+@pytest.mark.slow
+def test_config3_large_scale(pkg, oracle):
+    """Uniform 3-SAT n=1e6, m=4.3e6, B=16: one step from the seeded start
+    (the oracle needs seconds per step at this size)."""
+    cnf = uniform_ksat(1000000, 4300000, 3, seed=0)
+    check_bit_exact(oracle, cnf, 16, 1, 1e-4)
+
+
+# ------------------------------------------------------------ evaluate
+
+@pytest.mark.parametrize("nb", [1, 7, 33, 256])
+def test_evaluate_sparse_exact(pkg, oracle, nb):
+    import torch
+    cnf = zipf_weighted(2000, 9000, seed=4)
+    rng = np.random.default_rng(nb)
+    a01 = rng.integers(0, 2, size=(nb, cnf.n)).astype(np.uint8)
+    want = oracle.cost(cnf, a01)
+    pm1 = torch.from_numpy((2 * a01.astype(np.int8) - 1).T.copy()).cuda()
+    with pkg.Solver.from_cnf(cnf, restarts=1) as s:
+        got = s.evaluate(pm1, backend="sparse").cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------ autograd
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_autograd_loss_and_gradient(pkg, oracle, weighted):
+    """Configuration 3a: 3-SAT n=1000, m=4300; the autograd.Function's loss
+    and gradient against the oracle (FP64 within 1e-5, FP32-canon bit for
+    bit) and the oracle's central differences."""
+    import torch
+    cnf = uniform_ksat(1000, 4300, 3, seed=0)
+    if weighted:
+        cnf = Cnf(n=cnf.n, off=cnf.off, lits=cnf.lits,
+                  weights=(1 + np.arange(cnf.m) % 1000).astype(np.int64))
+    B = 4
+    x32 = oracle.init_x(cnf.n, B, 7)
+    r64 = oracle.objective_f64(cnf, x32.astype(np.float64))
+    r32 = oracle.objective_f32(cnf, x32)
+    with pkg.Solver.from_cnf(cnf, restarts=B) as s:
+        x = torch.from_numpy(x32).cuda().requires_grad_(True)
+        loss = pkg.msat_loss(x, s)
+        loss.sum().backward()
+        g = x.grad.cpu().numpy()
+        lv = loss.detach().cpu().numpy()
+    assert np.allclose(lv, r64["loss"], rtol=1e-5, atol=0)
+    tol = 1e-5 * np.abs(r64["grad"]).max(axis=0)
+    assert np.all(np.abs(g.astype(np.float64) - r64["grad"]) <= tol[None, :])
+    assert np.array_equal(g, r32["grad"])
+    # central differences of the FP64 objective at a few coordinates
+    h = 1e-6
+    x64 = x32.astype(np.float64)
+    for i, b in [(3, 0), (500, 1), (999, 3), (123, 2)]:
+        if abs(x64[i, b]) < 10 * h:
+            continue
+        xp = x64.copy(); xp[i, b] += h
+        xm = x64.copy(); xm[i, b] -= h
+        fd = (oracle.objective_f64(cnf, xp, want_grad=False)["loss"][b]
+              - oracle.objective_f64(cnf, xm, want_grad=False)["loss"][b]) / (2 * h)
+        assert abs(fd - g[i, b]) <= 1e-5 * np.abs(r64["grad"][:, b]).max() + 1e-9
+
+
+def test_autograd_gradient_scaling(pkg, oracle):
+    import torch
+    cnf = uniform_ksat(200, 860, 3, seed=3)
+    with pkg.Solver.from_cnf(cnf, restarts=2) as s:
+        x = torch.from_numpy(oracle.init_x(cnf.n, 2, 3)).cuda().requires_grad_(True)
+        loss = pkg.msat_loss(x, s)
+        (3.0 * loss[0] + 0.5 * loss[1]).backward()
+        g = x.grad.cpu().numpy()
+    r = oracle.objective_f32(cnf, oracle.init_x(cnf.n, 2, 3))
+    assert np.array_equal(g[:, 0], r["grad"][:, 0] * np.float32(3.0))
+    assert np.array_equal(g[:, 1], r["grad"][:, 1] * np.float32(0.5))
+
+
+# ---------------------------------------------------------- checkpoint
+
+def test_checkpoint_resume_is_bit_identical(pkg, oracle):
+    cnf = zipf_weighted(2000, 9000, seed=6)
+    with pkg.Solver.from_cnf(cnf, restarts=4, lr=1e-2) as a:
+        a.step(13, want_loss=False, want_cost=False)
+        st = a.get_state()
+        a.step(17, want_loss=False, want_cost=False)
+        xa = a.x()
+        ba = a.best()
+    with pkg.Solver.from_cnf(cnf, restarts=4, lr=1e-2, seed_x=99) as b:
+        b.set_state(st)
+        b.step(17, want_loss=False, want_cost=False)
+        xb = b.x()
+        bb = b.best()
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(ba[0], bb[0]) and np.array_equal(ba[1], bb[1])
+    ref = oracle.solve(cnf, 4, 1, 30, mode=oracle.MODE_F32, lr=1e-2)
+    assert np.array_equal(xb.astype(np.float64), ref["x_final"])
