@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the MaxSAT gradient engine: fwd+bwd literal-evals per second.
+
+One benchmark step is one iteration of Algorithm 1 for every restart of the
+workload: the clause pass (relaxed values, exact unsat cost, loss partials)
+and the variable pass (gradient over the transposed CSR, Adam, best
+assignment).  Work = nnz * B literal-evaluations per step (each literal of
+each restart is gathered forward and scattered backward once).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference]
+
+--impl reference times the CPU oracle on the same instance (a bounded
+sample per step).  Under torchrun every rank runs its own replica of the
+workload (the restarts and instances are independent; no collective on the
+data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import uniform_ksat, zipf_weighted  # noqa: E402
+
+L2_BYTES = 129 * 2 ** 20
+
+WORKLOADS = {
+    # name: (generator, restarts, description)
+    "ksat3_n5000_m21500_b256": (lambda: uniform_ksat(5000, 21500, 3, seed=0), 256,
+                                "uniform random 3-SAT, n=5000, m=21500 (seed 0), B=256 restarts, x from seed 1"),
+    "ksat3_n1000000_m4300000_b16": (lambda: uniform_ksat(1000000, 4300000, 3, seed=0), 16,
+                                    "uniform random 3-SAT, n=1e6, m=4.3e6 (seed 0), B=16 restarts"),
+    "zipf_n200000_m1000000_weighted_b1": (lambda: zipf_weighted(200000, 1000000, seed=0), 1,
+                                          "weighted MaxSAT, n=2e5, m=1e6, lengths 2+Geom(1/3)<=20, Zipf(1.2) variables, weights 1..1000, B=1"),
+    "ksat3_n50_m215_b1": (lambda: uniform_ksat(50, 215, 3, seed=0), 1,
+                          "uniform random 3-SAT, n=50, m=215 (seed 0), B=1"),
+}
+DEFAULT_WORKLOAD = "ksat3_n5000_m21500_b256"
+LR = 1e-4
+
+
+def algorithmic_bytes(cnf, B):
+    """Minimum bytes each kernel must move per launch."""
+    n, m, nnz = cnf.n, cnf.m, cnf.nnz
+    lens = np.diff(cnf.off)
+    uniform = m > 0 and bool(np.all(lens == lens[0]))
+    fwd = 4 * nnz + 4 * n * B + m * B / 8.0
+    if not uniform:
+        fwd += 4 * (m + 1)
+    if cnf.weights is not None:
+        fwd += 8 * m
+    bwd = 4 * (n + 1) + 4 * nnz + m * B / 8.0 + 24 * n * B + 4 * n * B
+    return {"forward": fwd, "backward": bwd}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 power=float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else None,
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["power"] is not None and r["power"] > 250.0] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_under_load": len(loaded)}
+
+
+def cpu_oracle_rate(cnf, B, budget_s=12.0, max_steps=200):
+    """Literal-evals/s of the FP32-mode oracle (Algorithm 1 on one host thread)."""
+    from oracle import oracle
+    oracle.build()
+    t = time.perf_counter()
+    oracle.solve(cnf, B, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+    one = max(time.perf_counter() - t, 1e-4)
+    steps = int(max(1, min(max_steps, budget_s / one)))
+    t = time.perf_counter()
+    oracle.solve(cnf, B, 1, steps, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+    dt = time.perf_counter() - t
+    # solve() also evaluates x_0 .. x_steps: steps updates + one extra evaluation
+    return cnf.nnz * B * steps / dt, steps, dt
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    gen, B, desc = WORKLOADS[args.workload]
+    cnf = gen()
+    from oracle import oracle
+    oracle.build()
+    # restarts are independent: a bounded sample of them per step keeps the
+    # whole run within a few minutes; the metric is per literal-evaluation
+    t = time.perf_counter()
+    oracle.solve(cnf, 1, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+    per_restart = max(time.perf_counter() - t, 1e-4)
+    b_sample = int(max(1, min(B, 20.0 / max(1, args.steps + args.warmup) / per_restart)))
+    for _ in range(args.warmup):
+        oracle.solve(cnf, b_sample, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.solve(cnf, b_sample, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = cnf.nnz * b_sample * args.steps / total
+    line = {
+        "impl": "reference", "metric": "fwd+bwd literal-evals/s", "value": value,
+        "unit": "literal-evals/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": cnf.n, "m": cnf.m,
+                   "nnz": cnf.nnz, "restarts": B, "restarts_per_step_sampled": b_sample},
+        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps, each one Algorithm 1 iteration (plus the "
+                                   f"evaluation of the next x) for {b_sample} of the {B} restarts, "
+                                   "FP32-mode C oracle, one host thread"},
+        "e2e": {"value": value, "unit": "literal-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2402_03640_gb300 as pkg
+    from paper_2402_03640_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    pkg_build.build()
+    pkg.load()
+    dev = torch.cuda.current_device()
+    gen, B, desc = WORKLOADS[args.workload]
+    cnf = gen()
+    nnz = cnf.nnz
+    work_per_step = nnz * B
+    abytes = algorithmic_bytes(cnf, B)
+    working_set = sum(abytes.values())
+    flush = working_set < 2 * L2_BYTES
+    flush_buf = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda") if flush else None
+
+    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        solver.step_async(1, final_eval=False)
+
+    # warm-up, then a short clock-settling run, both untimed
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_settle = time.perf_counter()
+    while time.perf_counter() - t_settle < 0.5:
+        for _ in range(20):
+            one_step()
+        torch.cuda.synchronize()
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        if flush:
+            flush_buf.zero_()
+        ev_s[k].record(stream)
+        one_step()
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    dev_ms = float(sum(step_ms))
+    t_max = dev_ms
+    units = float(work_per_step * args.steps)
+    if ws > 1:
+        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([units], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        units = float(u.item())
+    value = units / (t_max / 1e3)
+
+    # roofline of the dominant kernel, from the events around each launch
+    peak, peak_kind = measured_peaks()
+    per_kernel = {}
+    for kind in ("forward", "backward"):
+        launches, ms = prof[kind]
+        if launches:
+            avg = ms / launches
+            per_kernel[kind] = {"launches": launches, "avg_us": 1e3 * avg,
+                                "bytes": abytes[kind], "gbs": abytes[kind] / (avg / 1e3) / 1e9}
+    dom = max(per_kernel, key=lambda k: prof[k][1])
+    ach = per_kernel[dom]["gbs"]
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f)
+        ent = tr.get(args.workload, {}).get(dom)
+        if ent and ent.get("kernel_hash") == kernel_hash():
+            traffic = ent["bytes_per_launch"]
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic, "kernel": dom,
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                "algorithmic_bytes_per_launch": abytes[dom]}
+
+    # end to end through the public API with host buffers: upload the CNF
+    # from host memory, then per step the call a user makes (step plus the
+    # evaluation of the new x, loss and cost read back to the host)
+    torch.cuda.synchronize()
+    e2e_steps = args.steps
+    h2d = cnf.off.nbytes + cnf.lits.nbytes + (0 if cnf.weights is None else cnf.weights.nbytes)
+    t0 = time.perf_counter()
+    s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
+    for _ in range(e2e_steps):
+        s2.step(1)
+    t1 = time.perf_counter()
+    s2.close()
+    e2e_value = work_per_step * e2e_steps / (t1 - t0)
+    if ws > 1:
+        e = torch.tensor([t1 - t0], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
+        e2e_value = work_per_step * e2e_steps * ws / float(e.item())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, csteps, cdt = cpu_oracle_rate(cnf, B)
+        cpu = {"value": rate, "unit": "literal-evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"{csteps} Algorithm 1 steps of the FP32-mode C oracle on the full "
+                         f"instance, all {B} restarts, one host thread ({cdt:.1f} s)"}
+
+    launches = prof["forward"][0] + prof["backward"][0] + prof["evaluate"][0] + prof["other"][0]
+    info = solver.info()
+    _, cost = solver.step(0, want_loss=False)
+    line = {
+        "metric": "fwd+bwd literal-evals/s", "value": value, "unit": "literal-evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": cnf.n, "m": cnf.m,
+                   "nnz": nnz, "restarts": B, "lr": LR,
+                   "l2": ("flushed (256 MiB write) before every timed step" if flush
+                          else "working set larger than L2"),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "n_heavy": info["n_heavy"]},
+        "roofline": roofline,
+        "kernels": per_kernel,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "literal-evals/s", "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": B * (4 + 8),
+                "note": "msat_create from host arrays once, then per step msat_step(1) with the "
+                        "loss and cost copied back to host buffers"},
+        "gpu_launches": launches,
+        "wall_s_timed": wall1 - wall0,
+        "final_cost_min": int(cost.min()),
+    }
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_hash():
+    """Hash of the kernel sources, to tell whether stored ncu traffic is stale."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_03640_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -114,6 +114,16 @@ int msat_set_stream(msat_ctx *ctx, void *stream);
 int msat_step(msat_ctx *ctx, int32_t n_steps, float *loss_out, int64_t *cost_out);
 
 /*
+ * msat_step with flags.  MSAT_STEP_NO_FINAL_EVAL skips the evaluation of
+ * the final x; cost_out then holds the cost of the last x evaluated inside
+ * the loop (the x before the last update) and loss_out its loss.  With
+ * n_steps = 0 and this flag nothing runs.
+ */
+#define MSAT_STEP_NO_FINAL_EVAL 1u
+int msat_step_ex(msat_ctx *ctx, int32_t n_steps, uint32_t flags, float *loss_out,
+                 int64_t *cost_out);
+
+/*
  * Exact cost of a batch of assignments (Sec. 4, "Unsatisfiable Cores": a
  * clause is unsatisfied iff x'.W equals -len with x' read as +-1).
  *   assign_pm1  device int8[n][nb], entry (i, b) at i*nb + b: +1 = true,
@@ -187,6 +197,22 @@ int msat_get_state(msat_ctx *ctx, float *x, float *mom, float *vel, int64_t *bes
 int msat_set_state(msat_ctx *ctx, const float *x, const float *mom, const float *vel,
                    const int64_t *best_cost, const uint8_t *best_assign, int64_t steps_done,
                    const double *adam_pow);
+
+/*
+ * Kernel timing for benchmarks.  While enabled, every kernel the context
+ * launches is bracketed by CUDA events recorded on the context stream;
+ * msat_profile_read waits for the last event and returns, per kernel kind,
+ * the number of launches and their summed duration in milliseconds.
+ * Kinds: 0 forward clause pass, 1 backward variable pass (with Adam),
+ * 2 evaluation, 3 other (init, tanh, reductions).
+ */
+typedef struct {
+    int64_t launches[4];
+    double ms[4];
+} msat_profile;
+
+int msat_profile_enable(msat_ctx *ctx, int on);
+int msat_profile_read(msat_ctx *ctx, msat_profile *out, int reset);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *msat_last_error(void);

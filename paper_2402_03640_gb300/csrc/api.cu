@@ -54,7 +54,38 @@ struct msat_ctx {
     bool probe_ready = false;
     DevState PS{};
     DevStep PD{};
+
+    // kernel timing (msat_profile_*): event pairs around each launch
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used = 0;
 };
+
+enum { PROF_FWD = 0, PROF_BWD = 1, PROF_EVAL = 2, PROF_OTHER = 3 };
+
+static void prof_begin(msat_ctx *c, int kind) {
+    if (!c->prof_on) return;
+    if (2 * c->prof_used + 2 > c->prof_ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            cudaGetLastError();
+            c->prof_on = false;
+            return;
+        }
+        c->prof_ev.push_back(a);
+        c->prof_ev.push_back(b);
+        c->prof_kind.push_back(kind);
+    }
+    c->prof_kind[c->prof_used] = kind;
+    cudaEventRecord(c->prof_ev[2 * c->prof_used], c->stream);
+}
+
+static void prof_end(msat_ctx *c) {
+    if (!c->prof_on) return;
+    cudaEventRecord(c->prof_ev[2 * c->prof_used + 1], c->stream);
+    ++c->prof_used;
+}
 
 static int dalloc(msat_ctx *c, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -78,6 +109,10 @@ static int dalloc_t(msat_ctx *c, T **p, size_t count) {
 static void free_all(msat_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_kind.clear();
+    c->prof_used = 0;
 }
 
 extern "C" int msat_config_default(msat_config *cfg) {
@@ -331,23 +366,34 @@ extern "C" int msat_set_stream(msat_ctx *c, void *stream) {
 
 // One evaluation of the current x (final evaluation of a msat_step call).
 static cudaError_t eval_current(msat_ctx *c) {
+    prof_begin(c, PROF_FWD);
     cudaError_t e = launch_forward(c->I, c->S, c->D, FWD_EVAL, nullptr, c->stream);
+    prof_end(c);
     if (e) return e;
-    return launch_backward(c->I, c->S, c->D, BWD_BITS_ONLY, nullptr, nullptr, nullptr, nullptr,
-                           c->stream);
+    prof_begin(c, PROF_BWD);
+    e = launch_backward(c->I, c->S, c->D, BWD_BITS_ONLY, nullptr, nullptr, nullptr, nullptr,
+                        c->stream);
+    prof_end(c);
+    return e;
 }
 
-extern "C" int msat_step(msat_ctx *c, int32_t n_steps, float *loss_out, int64_t *cost_out) {
+extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float *loss_out,
+                            int64_t *cost_out) {
     if (!c) return fail(MSAT_EINVAL, "msat_step: ctx is NULL");
     if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
+    if (flags & ~MSAT_STEP_NO_FINAL_EVAL) return fail(MSAT_EINVAL, "msat_step: unknown flags");
     cudaError_t e = cudaSuccess;
     for (int32_t s = 0; s < n_steps && !e; ++s) {
+        prof_begin(c, PROF_FWD);
         e = launch_forward(c->I, c->S, c->D, FWD_STEP, nullptr, c->stream);
-        if (!e)
-            e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, nullptr,
-                                c->stream);
+        prof_end(c);
+        if (e) break;
+        prof_begin(c, PROF_BWD);
+        e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, nullptr,
+                            c->stream);
+        prof_end(c);
     }
-    if (!e) e = eval_current(c);
+    if (!e && !(flags & MSAT_STEP_NO_FINAL_EVAL)) e = eval_current(c);
     if (e) return cuda_fail(e, "msat_step: kernel launch");
     c->steps_done_host += n_steps;
     if (loss_out)
@@ -360,13 +406,40 @@ extern "C" int msat_step(msat_ctx *c, int32_t n_steps, float *loss_out, int64_t 
     return MSAT_OK;
 }
 
+extern "C" int msat_step(msat_ctx *c, int32_t n_steps, float *loss_out, int64_t *cost_out) {
+    return msat_step_ex(c, n_steps, 0u, loss_out, cost_out);
+}
+
+extern "C" int msat_profile_enable(msat_ctx *c, int on) {
+    if (!c) return fail(MSAT_EINVAL, "msat_profile_enable: ctx is NULL");
+    c->prof_on = on != 0;
+    return MSAT_OK;
+}
+
+extern "C" int msat_profile_read(msat_ctx *c, msat_profile *out, int reset) {
+    if (!c || !out) return fail(MSAT_EINVAL, "msat_profile_read: NULL argument");
+    memset(out, 0, sizeof(*out));
+    if (c->prof_used) MSAT_CUDA_TRY(cudaEventSynchronize(c->prof_ev[2 * c->prof_used - 1]));
+    for (size_t k = 0; k < c->prof_used; ++k) {
+        float ms = 0.0f;
+        MSAT_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
+        const int kind = c->prof_kind[k];
+        out->launches[kind] += 1;
+        out->ms[kind] += ms;
+    }
+    if (reset) c->prof_used = 0;
+    return MSAT_OK;
+}
+
 extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
                              int32_t backend) {
     if (!c) return fail(MSAT_EINVAL, "msat_evaluate: ctx is NULL");
     if (nb < 1 || !assign_pm1 || !cost_out)
         return fail(MSAT_EINVAL, "msat_evaluate: need nb >= 1 and non-NULL buffers");
     if (backend == MSAT_BACKEND_SPARSE) {
+        prof_begin(c, PROF_EVAL);
         cudaError_t e = launch_eval_sparse(c->I, assign_pm1, nb, (long long *)cost_out, c->stream);
+        prof_end(c);
         if (e) return cuda_fail(e, "msat_evaluate: sparse kernel");
         return MSAT_OK;
     }

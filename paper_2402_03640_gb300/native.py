@@ -49,6 +49,13 @@ class msat_info(ctypes.Structure):
                 ("uniform_len", ctypes.c_int32)]
 
 
+class msat_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4)]
+
+
+STEP_NO_FINAL_EVAL = 1
+PROFILE_KINDS = ("forward", "backward", "evaluate", "other")
+
 _lock = threading.Lock()
 _lib = None
 
@@ -86,6 +93,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_get_info": ([P, P], ctypes.c_int),
             "msat_get_state": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "msat_set_state": ([P, P, P, P, P, P, i64, P], ctypes.c_int),
+            "msat_step_ex": ([P, i32, ctypes.c_uint32, P, P], ctypes.c_int),
+            "msat_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
+            "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),
             "msat_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():

@@ -103,8 +103,19 @@ class Solver:
         check(self._lib.msat_step(self._ctx, int(n_steps), _p(loss), _p(cost)))
         return loss, cost
 
-    def step_async(self, n_steps: int) -> None:
-        check(self._lib.msat_step(self._ctx, int(n_steps), None, None))
+    def step_async(self, n_steps: int, final_eval: bool = True) -> None:
+        flags = 0 if final_eval else native.STEP_NO_FINAL_EVAL
+        check(self._lib.msat_step_ex(self._ctx, int(n_steps), flags, None, None))
+
+    def profile(self, on: bool = True) -> None:
+        """Bracket every kernel of this context with CUDA events."""
+        check(self._lib.msat_profile_enable(self._ctx, int(bool(on))))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kind: (launches, total ms)} for kinds forward, backward, evaluate, other."""
+        p = native.msat_profile()
+        check(self._lib.msat_profile_read(self._ctx, ctypes.byref(p), int(bool(reset))))
+        return {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(native.PROFILE_KINDS)}
 
     def best(self) -> Tuple[np.ndarray, np.ndarray]:
         a = np.empty((self.B, self.n), np.uint8)
