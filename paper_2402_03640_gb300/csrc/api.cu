@@ -220,16 +220,44 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     for (int32_t i = 0; i < n_vars; ++i) max_deg = std::max(max_deg, voff[(size_t)i + 1] - voff[(size_t)i]);
     if ((int64_t)max_deg > 4095LL * 32 * kChunk)
         return fail(MSAT_EINVAL, "msat_create: a variable occurs more than 4095*32768 times");
-    // variables whose occurrence sum is split into 1024-occurrence chunks
-    const int32_t heavy_deg = 64;
+    const int32_t B = cfg.restarts;
+    const int VW = (B % 4 == 0) ? 4 : (B % 2 == 0 ? 2 : 1);
+    const int G = B / VW;
+    // light blocks stage occ_cap occurrence rows of B floats in shared memory;
+    // a variable with more occurrences is split into 1024-occurrence chunks
+    const int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
+    const int32_t heavy_deg = occ_cap;
     std::vector<int32_t> hvar, hchunk0(1, 0);
-    for (int32_t i = 0; i < n_vars; ++i) {
-        const int32_t d = voff[(size_t)i + 1] - voff[(size_t)i];
-        if (d > heavy_deg) {
-            hvar.push_back(i);
-            hchunk0.push_back(hchunk0.back() + (d + kChunk - 1) / kChunk);
+    std::vector<int2> lblk;
+    {
+        const int32_t vmax = kThreads / G;
+        int32_t v0 = -1, cnt = 0, occ_in = 0;
+        for (int32_t i = 0; i < n_vars; ++i) {
+            const int32_t d = voff[(size_t)i + 1] - voff[(size_t)i];
+            if (d > heavy_deg) {
+                hvar.push_back(i);
+                hchunk0.push_back(hchunk0.back() + (d + kChunk - 1) / kChunk);
+                if (v0 >= 0) lblk.push_back(make_int2(v0, i));
+                v0 = -1;
+                continue;
+            }
+            if (v0 >= 0 && (cnt == vmax || occ_in + d > occ_cap)) {
+                lblk.push_back(make_int2(v0, i));
+                v0 = -1;
+            }
+            if (v0 < 0) {
+                v0 = i;
+                cnt = 0;
+                occ_in = 0;
+            }
+            ++cnt;
+            occ_in += d;
         }
+        if (v0 >= 0) lblk.push_back(make_int2(v0, n_vars));
     }
+    // f of the clause pass is kept when the [m][B] array is small; otherwise
+    // the variable pass recomputes f of unsatisfied clauses
+    const bool use_fstore = (double)m * B * sizeof(float) <= 96.0 * (1 << 20) || B <= 2;
 
     msat_ctx *c = new (std::nothrow) msat_ctx();
     if (!c) return fail(MSAT_ENOMEM, "msat_create: host allocation failed");
@@ -245,13 +273,11 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     c->max_deg = max_deg;
     c->wsum = wsum;
 
-    const int32_t B = c->B;
     const int64_t nB = (int64_t)n_vars * B;
-    const int VW = (B % 4 == 0) ? 4 : (B % 2 == 0 ? 2 : 1);
-    const int G = B / VW;
     int rc = MSAT_OK;
     int32_t *d_coff = nullptr, *d_lit = nullptr, *d_voff = nullptr, *d_occ = nullptr;
     int32_t *d_hvar = nullptr, *d_hch = nullptr;
+    int2 *d_lblk = nullptr;
     int64_t *d_w = nullptr;
 #define TRY_ALLOC(ptr, count)                          \
     do {                                               \
@@ -265,6 +291,8 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     TRY_ALLOC(d_occ, nnz);
     TRY_ALLOC(d_hvar, (int64_t)hvar.size());
     TRY_ALLOC(d_hch, (int64_t)hchunk0.size());
+    TRY_ALLOC(d_lblk, (int64_t)lblk.size());
+    if (use_fstore) TRY_ALLOC(c->S.fstore, m * B);
     TRY_ALLOC(c->S.x, nB);
     TRY_ALLOC(c->S.mom, nB);
     TRY_ALLOC(c->S.vel, nB);
@@ -288,11 +316,14 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     I.heavy_chunks = hchunk0.back();
     I.heavy_var = d_hvar;
     I.heavy_chunk0 = d_hch;
+    I.n_lblk = (int32_t)lblk.size();
+    I.occ_cap = occ_cap;
+    I.lblk = d_lblk;
 
     DevStep &D = c->D;
     D.fwd_blocks = fwd_grid_blocks(I);
     TRY_ALLOC(D.sc, 1);
-    TRY_ALLOC(D.wu_acc, B);
+    TRY_ALLOC(D.wu_acc, (int64_t)kRep * B);
     TRY_ALLOC(D.cost, B);
     TRY_ALLOC(D.best, B);
     TRY_ALLOC(D.improved, B);
@@ -331,9 +362,10 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     if (!e) e = up(d_occ, occ.data(), sizeof(int32_t) * occ.size());
     if (!e) e = up(d_hvar, hvar.data(), sizeof(int32_t) * hvar.size());
     if (!e) e = up(d_hch, hchunk0.data(), sizeof(int32_t) * hchunk0.size());
+    if (!e) e = up(d_lblk, lblk.data(), sizeof(int2) * lblk.size());
     if (!e) e = up(D.sc, &sc, sizeof(sc));
     if (!e) e = up(D.best, best.data(), sizeof(long long) * best.size());
-    if (!e) e = cudaMemsetAsync(D.wu_acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (!e) e = cudaMemsetAsync(D.wu_acc, 0, sizeof(unsigned long long) * (size_t)kRep * B, st);
     if (!e) e = cudaMemsetAsync(D.improved, 0, sizeof(int) * (size_t)B, st);
     if (!e) e = cudaMemsetAsync(D.cost, 0, sizeof(long long) * (size_t)B, st);
     if (!e) e = cudaMemsetAsync(D.loss, 0, sizeof(float) * (size_t)B, st);
@@ -371,8 +403,7 @@ static cudaError_t eval_current(msat_ctx *c) {
     prof_end(c);
     if (e) return e;
     prof_begin(c, PROF_BWD);
-    e = launch_backward(c->I, c->S, c->D, BWD_BITS_ONLY, nullptr, nullptr, nullptr, nullptr,
-                        c->stream);
+    e = launch_backward(c->I, c->S, c->D, BWD_BITS_ONLY, nullptr, nullptr, nullptr, c->stream);
     prof_end(c);
     return e;
 }
@@ -389,8 +420,7 @@ extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float 
         prof_end(c);
         if (e) break;
         prof_begin(c, PROF_BWD);
-        e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, nullptr,
-                            c->stream);
+        e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, c->stream);
         prof_end(c);
     }
     if (!e && !(flags & MSAT_STEP_NO_FINAL_EVAL)) e = eval_current(c);
@@ -562,7 +592,8 @@ static int ensure_probe(msat_ctx *c) {
     c->PS.t1 = c->PS.t0;
     if ((rc = dalloc_t(c, &c->PS.ubits, (c->m * B + 31) / 32 + 1))) return rc;
     if ((rc = dalloc_t(c, &c->PD.sc, 1))) return rc;
-    if ((rc = dalloc_t(c, &c->PD.wu_acc, B))) return rc;
+    if ((rc = dalloc_t(c, &c->PD.wu_acc, (int64_t)kRep * B))) return rc;
+    if (c->S.fstore && (rc = dalloc_t(c, &c->PS.fstore, c->m * B))) return rc;
     if ((rc = dalloc_t(c, &c->PD.cost, B))) return rc;
     if ((rc = dalloc_t(c, &c->PD.cscale, B))) return rc;
     if ((rc = dalloc_t(c, &c->PD.lpart, (int64_t)c->PD.fwd_blocks * B))) return rc;
@@ -574,7 +605,7 @@ static int ensure_probe(msat_ctx *c) {
     sc.counter = 0;
     sc.steps_done = 0;
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->PD.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
-    MSAT_CUDA_TRY(cudaMemsetAsync(c->PD.wu_acc, 0, sizeof(unsigned long long) * (size_t)B, c->stream));
+    MSAT_CUDA_TRY(cudaMemsetAsync(c->PD.wu_acc, 0, sizeof(unsigned long long) * (size_t)kRep * B, c->stream));
     MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->probe_ready = true;
     return MSAT_OK;
@@ -602,8 +633,8 @@ extern "C" int msat_backward(msat_ctx *c, const float *gscale, float *grad) {
     if (!c || !grad) return fail(MSAT_EINVAL, "msat_backward: NULL argument");
     if (!c->probe_ready) return fail(MSAT_ESTATE, "msat_backward: no msat_forward before it");
     // 1 - t^2 comes from the tanh(x) stored by msat_forward
-    cudaError_t e = launch_backward(c->I, c->PS, c->PD, BWD_GRAD_ONLY, nullptr, c->PS.t0, gscale,
-                                    grad, c->stream);
+    cudaError_t e = launch_backward(c->I, c->PS, c->PD, BWD_GRAD_ONLY, c->PS.t0, gscale, grad,
+                                    c->stream);
     if (e) return cuda_fail(e, "msat_backward");
     return MSAT_OK;
 }

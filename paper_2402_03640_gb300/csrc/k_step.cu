@@ -136,71 +136,69 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
     }
 }
 
-// Occurrence term of clause j (occurrence sign neg) for VW restarts:
-// +-((float)w_j * f_j) * (2/W_U) where clause j is unsat, +0 elsewhere.
-template <int VW>
-__device__ __forceinline__ void occ_term(const DevInst &I, int kfix, const float *__restrict__ t,
-                                         const uint32_t *__restrict__ ubits,
-                                         const float (&cs)[VW], int o, int col,
-                                         float (&term)[VW]) {
+// Fixed-length clause (KFIX literals): all literal loads first, then all
+// row gathers, so the loads of one clause are in flight together.
+template <int VW, int KFIX>
+__device__ __forceinline__ void clause_value_fixed(const DevInst &I, const float *__restrict__ t,
+                                                   int j, int col, float (&f)[VW],
+                                                   bool (&sat)[VW]) {
     const int B = I.B;
-    const int j = o >> 1;
-    const bool neg = o & 1;
-    const int64_t qb = (int64_t)j * B + col;
-    const uint32_t wd = __ldg(ubits + (qb >> 5));
-    const uint32_t nib = (wd >> (qb & 31)) & ((1u << VW) - 1u);
+    int L[KFIX];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) term[e] = 0.0f;
-    if (nib) {
-        int beg, end;
-        clause_range(I, kfix, j, beg, end);
-        float f[VW];
-        bool sat[VW];
-        clause_value<VW, false>(I, t, beg, end, col, f, sat);
-        const float wj = I.w ? (float)__ldg(I.w + j) : 1.0f;
+    for (int p = 0; p < KFIX; ++p) L[p] = __ldg(I.lit + j * KFIX + p);
+    float tv[KFIX][VW];
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            if ((nib >> e) & 1u) {
-                float g = (wj * f[e]) * cs[e];
-                term[e] = neg ? -g : g;
-            }
+    for (int p = 0; p < KFIX; ++p) ldv<VW>(t + (int64_t)(L[p] >> 1) * B + col, tv[p]);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        sat[e] = false;
+#pragma unroll
+        for (int p = 0; p < KFIX; ++p) {
+            const bool neg = L[p] & 1;
+            const float term = neg ? -tv[p][e] : tv[p][e];
+            f[e] = (p == 0) ? term : f[e] + term;
+            sat[e] |= ((tv[p][e] > 0.0f) != neg);
         }
     }
 }
 
-// Canonical occurrence sum of a variable with occurrences [beg, end) in one
-// thread: 32-term leaves in order, leaves combined by the dyadic counter.
-template <int VW>
-__device__ __forceinline__ void occ_sum_thread(const DevInst &I, int kfix,
-                                               const float *__restrict__ t,
-                                               const uint32_t *__restrict__ ubits,
-                                               const float (&cs)[VW], int beg, int end, int col,
-                                               float (&S)[VW]) {
-    LeafCounter<6> lc[VW];
-    float leaf[VW];
+// Occurrence term for VW restarts given the occurrence word o = j << 1 | neg
+// and the unsat word covering (j, col): +-((float)w_j * f_j) * (2/W_U) where
+// clause j is unsat, +0 elsewhere.  f comes from the clause pass's store when
+// there is one, else it is recomputed from the clause in the same order.
+template <int VW, int KFIX>
+__device__ __forceinline__ void occ_term(const DevInst &I, int kfix, const float *__restrict__ t,
+                                         const float *__restrict__ fstore, const float (&cs)[VW],
+                                         int o, uint32_t wd, int col, float (&term)[VW]) {
+    const int B = I.B;
+    const int j = o >> 1;
+    const bool neg = o & 1;
+    const int64_t qb = (int64_t)j * B + col;
+    const uint32_t nib = (wd >> (qb & 31)) & ((1u << VW) - 1u);
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        lc[e].init();
-        leaf[e] = 0.0f;
-    }
-    int in_leaf = 0;
-    for (int s = beg; s < end; ++s) {
-        float term[VW];
-        occ_term<VW>(I, kfix, t, ubits, cs, __ldg(I.occ + s), col, term);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) leaf[e] = (in_leaf == 0) ? term[e] : leaf[e] + term[e];
-        if (++in_leaf == 32) {
-#pragma unroll
-            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
-            in_leaf = 0;
+    for (int e = 0; e < VW; ++e) term[e] = 0.0f;
+    if (!nib) return;
+    float f[VW];
+    if (fstore) {
+        ldv<VW>(fstore + qb, f);
+    } else {
+        bool sat[VW];
+        if constexpr (KFIX > 0) {
+            clause_value_fixed<VW, KFIX>(I, t, j, col, f, sat);
+        } else {
+            int beg, end;
+            clause_range(I, kfix, j, beg, end);
+            clause_value<VW, false>(I, t, beg, end, col, f, sat);
         }
     }
-    if (in_leaf) {
+    const float wj = I.w ? (float)__ldg(I.w + j) : 1.0f;
 #pragma unroll
-        for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+    for (int e = 0; e < VW; ++e) {
+        if ((nib >> e) & 1u) {
+            const float g = (wj * f[e]) * cs[e];
+            term[e] = neg ? -g : g;
+        }
     }
-#pragma unroll
-    for (int e = 0; e < VW; ++e) S[e] = lc[e].finish();
 }
 
 // Dyadic tree over the first K lanes' values (lane 0 receives the result).
@@ -226,6 +224,12 @@ __device__ __forceinline__ float adam_update(const AdamView &A, float x, float &
     v = vq;
     return x - (A.a_t * mq) / den;
 }
+
+template <int VW>
+struct LightLevels {
+    // occurrence rows of one light block / 32, rounded up to a power of two
+    static constexpr int value = VW == 1 ? 9 : (VW == 2 ? 8 : 7);
+};
 
 }  // namespace
 
@@ -274,11 +278,16 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 }
 
 // --------------------------------------------------------------- k_forward
+// One item = (clause j, restart group g).  A warp takes 64 consecutive items
+// per iteration (two per lane), so the loads of two clauses are in flight
+// together; the unsat bits of 32 consecutive items are packed with shuffles
+// into whole 32-bit words.
 
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
     k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
-              const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits, int mode) {
+              const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
+              float *__restrict__ fstore, int mode) {
     __shared__ unsigned long long s_w[kThreads * VW];
     __shared__ float s_l[kThreads * VW];
     __shared__ int s_last;
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(kThreads)
     const int g = threadIdx.x % G;
     const int col = g * VW;
     const long long total = (long long)I.m * G;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long stride = 2LL * gridDim.x * blockDim.x;
 
     float lacc[VW];
     unsigned long long wacc[VW];
@@ -302,33 +311,68 @@ __global__ void __launch_bounds__(kThreads)
         wacc[e] = 0ull;
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+    for (long long base = 2LL * blockIdx.x * blockDim.x + 2 * (threadIdx.x & ~31); base < total;
          base += stride) {
-        const long long item = base + lane;
-        const bool active = item < total;
-        unsigned nib = 0;
-        if (active) {
-            const int j = (int)(item / G);
-            int beg, end;
-            clause_range(I, kfix, j, beg, end);
-            float f[VW];
-            bool sat[VW];
-            clause_value<VW, true>(I, t, beg, end, col, f, sat);
-            const long long wj = I.w ? __ldg(I.w + j) : 1ll;
-            const float wf = (float)wj;
+        long long item[2] = {base + lane, base + 32 + lane};
+        bool act[2] = {item[0] < total, item[1] < total};
+        int jj[2] = {act[0] ? (int)(item[0] / G) : 0, act[1] ? (int)(item[1] / G) : 0};
+        float f[2][VW];
+        bool sat[2][VW];
+        if constexpr (KFIX > 0) {
+            // both clauses' literals, then both clauses' rows
+            int L[2][KFIX];
 #pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                if (!sat[e]) {
-                    nib |= 1u << e;
-                    wacc[e] += (unsigned long long)wj;
-                    lacc[e] += (wf * f[e]) * f[e];
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p < KFIX; ++p) L[h][p] = __ldg(I.lit + jj[h] * KFIX + p);
+            float tv[2][KFIX][VW];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p < KFIX; ++p)
+                    ldv<VW>(t + (int64_t)(L[h][p] >> 1) * B + col, tv[h][p]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    sat[h][e] = false;
+#pragma unroll
+                    for (int p = 0; p < KFIX; ++p) {
+                        const bool neg = L[h][p] & 1;
+                        const float term = neg ? -tv[h][p][e] : tv[h][p][e];
+                        f[h][e] = (p == 0) ? term : f[h][e] + term;
+                        sat[h][e] |= ((tv[h][p][e] > 0.0f) != neg);
+                    }
                 }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int beg = 0, end = 0;
+                if (act[h]) clause_range(I, kfix, jj[h], beg, end);
+                clause_value<VW, true>(I, t, beg, end, col, f[h], sat[h]);
             }
         }
-        unsigned word = nib << ((lane % LPW) * VW);
 #pragma unroll
-        for (int o = 1; o < LPW; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-        if (active && (lane % LPW) == 0) ubits[(item * VW) >> 5] = word;
+        for (int h = 0; h < 2; ++h) {
+            unsigned nib = 0;
+            if (act[h]) {
+                const long long wj = I.w ? __ldg(I.w + jj[h]) : 1ll;
+                const float wf = (float)wj;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    if (!sat[h][e]) {
+                        nib |= 1u << e;
+                        wacc[e] += (unsigned long long)wj;
+                        lacc[e] += (wf * f[h][e]) * f[h][e];
+                    }
+                }
+                if (fstore) stv<VW>(fstore + (int64_t)jj[h] * B + col, f[h]);
+            }
+            unsigned word = nib << ((lane % LPW) * VW);
+#pragma unroll
+            for (int o = 1; o < LPW; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
+            if (act[h] && (lane % LPW) == 0) ubits[(item[h] * VW) >> 5] = word;
+        }
     }
 
 #pragma unroll
@@ -338,6 +382,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
     if (threadIdx.x < G) {
+        unsigned long long *acc = D.wu_acc + (long long)(blockIdx.x % kRep) * B;
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             unsigned long long sw = 0;
@@ -347,7 +392,7 @@ __global__ void __launch_bounds__(kThreads)
                 sl += s_l[r * VW + e];
             }
             const int b = threadIdx.x * VW + e;
-            if (sw) atomicAdd(D.wu_acc + b, sw);
+            if (sw) atomicAdd(acc + b, sw);
             D.lpart[(long long)blockIdx.x * B + b] = sl;
         }
     }
@@ -358,7 +403,9 @@ __global__ void __launch_bounds__(kThreads)
     if (!s_last) return;
     __threadfence();
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        const long long c = (long long)atomicExch(D.wu_acc + b, 0ull);
+        unsigned long long wu = 0;
+        for (int r = 0; r < kRep; ++r) wu += atomicExch(D.wu_acc + (long long)r * B + b, 0ull);
+        const long long c = (long long)wu;
         D.cost[b] = c;
         if (mode != FWD_PROBE) {
             const long long bb = D.best[b];
@@ -386,7 +433,7 @@ __global__ void __launch_bounds__(kThreads)
 int fwd_grid_blocks(const DevInst &I) {
     const int VW = (I.B % 4 == 0) ? 4 : (I.B % 2 == 0 ? 2 : 1);
     const long long items = (long long)I.m * (I.B / VW);
-    long long blocks = (items + kThreads - 1) / kThreads;
+    long long blocks = (items + 2 * kThreads - 1) / (2 * kThreads);
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
@@ -394,30 +441,38 @@ int fwd_grid_blocks(const DevInst &I) {
 
 template <int VW>
 static cudaError_t launch_forward_vw(const DevInst &I, const DevState &S, const DevStep &D,
-                                     int mode, const float *t_ovr, uint32_t *ubits,
-                                     cudaStream_t st) {
+                                     int mode, const float *t_ovr, cudaStream_t st) {
     const int blocks = D.fwd_blocks;
     if (I.kfix == 3)
-        k_forward<VW, 3><<<blocks, kThreads, 0, st>>>(I, S.t0, S.t1, t_ovr, D, ubits, mode);
+        k_forward<VW, 3><<<blocks, kThreads, 0, st>>>(I, S.t0, S.t1, t_ovr, D, S.ubits, S.fstore, mode);
     else
-        k_forward<VW, 0><<<blocks, kThreads, 0, st>>>(I, S.t0, S.t1, t_ovr, D, ubits, mode);
+        k_forward<VW, 0><<<blocks, kThreads, 0, st>>>(I, S.t0, S.t1, t_ovr, D, S.ubits, S.fstore, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st) {
-    if (I.B % 4 == 0) return launch_forward_vw<4>(I, S, D, mode, t_override, S.ubits, st);
-    if (I.B % 2 == 0) return launch_forward_vw<2>(I, S, D, mode, t_override, S.ubits, st);
-    return launch_forward_vw<1>(I, S, D, mode, t_override, S.ubits, st);
+    if (I.B % 4 == 0) return launch_forward_vw<4>(I, S, D, mode, t_override, st);
+    if (I.B % 2 == 0) return launch_forward_vw<2>(I, S, D, mode, t_override, st);
+    return launch_forward_vw<1>(I, S, D, mode, t_override, st);
 }
 
 // -------------------------------------------------------------- k_backward
+// k_backward_heavy: variables with more occurrences than a light block can
+// stage, one warp per (1024-occurrence chunk, restart group); the last warp
+// of a (variable, group) combines the chunk partials in the fixed tree order
+// and applies the update.
+// k_backward_light: one block per range of consecutive light variables.
+// Phase 1 spreads the block's (occurrence, restart group) items over all
+// threads and stages each occurrence term in shared memory; phase 2 gives
+// each (variable, restart group) to one thread, which sums its terms in the
+// fixed order and applies 1 - t^2 and Adam.  Block b < B also reduces the
+// loss of restart b from the forward partials.
 
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
-    k_backward(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ x_ovr,
-               const float *__restrict__ t_ovr, const float *__restrict__ gscale,
-               float *__restrict__ grad_out, int heavy_blocks) {
+    k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
     const int B = I.B;
     const int G = B / VW;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
@@ -430,29 +485,8 @@ __global__ void __launch_bounds__(kThreads)
     } else {
         tcur = t_ovr;
     }
-    const float *xin = x_ovr ? x_ovr : S.x;
     const uint32_t *__restrict__ ubits = S.ubits;
-
-    // loss of the evaluated x per restart, from the forward block partials
-    if (mode == BWD_UPDATE) {
-        __shared__ float s_red[kThreads];
-        for (int b = blockIdx.x; b < B; b += gridDim.x) {
-            float acc = 0.0f;
-            for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
-                acc += D.lpart[(long long)k * B + b];
-            s_red[threadIdx.x] = acc;
-            __syncthreads();
-            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-                if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                const long long c = D.cost[b];
-                D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
-            }
-            __syncthreads();
-        }
-    }
+    const float *__restrict__ fstore = S.fstore;
 
     AdamView A;
     {
@@ -466,17 +500,16 @@ __global__ void __launch_bounds__(kThreads)
         A.eps = sc->epsf;
     }
 
-    if ((int)blockIdx.x < heavy_blocks) {
+    {
         // ---------------- heavy variables: one warp per (chunk, restart group)
         const int lane = threadIdx.x & 31;
         const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const long long nwarps = ((long long)heavy_blocks * blockDim.x) >> 5;
-        const long long nchunks = I.n_heavy > 0 ? __ldg(I.heavy_chunk0 + I.n_heavy) : 0;
+        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        const long long nchunks = I.heavy_chunks;
         for (long long it = warp; it < nchunks * G; it += nwarps) {
             const int gg = (int)(it % G);
             const long long cidx = it / G;
             const int col = gg * VW;
-            // heavy variable owning chunk cidx
             int lo = 0, hi = I.n_heavy - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
@@ -498,8 +531,10 @@ __global__ void __launch_bounds__(kThreads)
                 const int lb = vbeg + c * kChunk + lane * 32;
                 const int le = min(lb + 32, vend);
                 for (int s = lb; s < le; ++s) {
+                    const int o = __ldg(I.occ + s);
+                    const uint32_t wd = __ldg(ubits + (((int64_t)(o >> 1) * B + col) >> 5));
                     float term[VW];
-                    occ_term<VW>(I, kfix, tcur, ubits, cs, __ldg(I.occ + s), col, term);
+                    occ_term<VW, KFIX>(I, kfix, tcur, fstore, cs, o, wd, col, term);
 #pragma unroll
                     for (int e = 0; e < VW; ++e) leaf[e] = (s == lb) ? term[e] : leaf[e] + term[e];
                 }
@@ -541,7 +576,7 @@ __global__ void __launch_bounds__(kThreads)
                 D.hcount[(long long)h * G + gg] = 0;
                 const int64_t q0 = (int64_t)i * B + col;
                 float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-                if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(xin + q0, xv);
+                if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
                 if (mode == BWD_BITS_ONLY) {
 #pragma unroll
                     for (int e = 0; e < VW; ++e)
@@ -579,102 +614,219 @@ __global__ void __launch_bounds__(kThreads)
         return;
     }
 
-    // -------------------- light variables: one thread per (variable, group)
-    const int lblock = blockIdx.x - heavy_blocks;
-    const int lblocks = gridDim.x - heavy_blocks;
-    const int g = threadIdx.x % G;
+}
+
+template <int VW, int KFIX>
+__global__ void __launch_bounds__(kThreads)
+    k_backward_light(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
+    extern __shared__ float4 dyn_smem[];
+    const int B = I.B;
+    const int G = B / VW;
+    const int kfix = KFIX > 0 ? KFIX : I.kfix;
+    const long long steps = D.sc->steps_done;
+    const float *tcur;
+    float *tnext = nullptr;
+    if (mode == BWD_UPDATE) {
+        tcur = ((steps - 1) & 1) ? S.t1 : S.t0;
+        tnext = (steps & 1) ? S.t1 : S.t0;
+    } else {
+        tcur = t_ovr;
+    }
+    const uint32_t *__restrict__ ubits = S.ubits;
+    const float *__restrict__ fstore = S.fstore;
+
+    // loss of the evaluated x per restart, from the forward block partials
+    if (mode == BWD_UPDATE) {
+        __shared__ float s_red[kThreads];
+        for (int b = blockIdx.x; b < B; b += gridDim.x) {
+            float acc = 0.0f;
+            for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
+                acc += D.lpart[(long long)k * B + b];
+            s_red[threadIdx.x] = acc;
+            __syncthreads();
+            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+                if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const long long c = D.cost[b];
+                D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
+            }
+            __syncthreads();
+        }
+    }
+
+    AdamView A;
+    {
+        const StepScalars *sc = D.sc;
+        A.a_t = sc->a_t;
+        A.r_t = sc->r_t;
+        A.b1 = sc->b1f;
+        A.b2 = sc->b2f;
+        A.omb1 = sc->omb1f;
+        A.omb2 = sc->omb2f;
+        A.eps = sc->epsf;
+    }
+
+    // ------------------------------------------------------- light block
+    float *sterm = reinterpret_cast<float *>(dyn_smem);
+    if ((int)blockIdx.x >= I.n_lblk) return;  // a grid of one block when every variable is heavy
+    const int2 rg = I.lblk[blockIdx.x];
+    const int v0 = rg.x, v1 = rg.y;
+    const int s0 = __ldg(I.voff + v0);
+    const int nocc = __ldg(I.voff + v1) - s0;
+    const int gshift = __ffs(G) - 1;  // G is a power of two
+    const int g = threadIdx.x & (G - 1);
     const int col = g * VW;
-    float cs[VW], gsc[VW];
-    bool upd[VW], imp[VW];
+    float cs[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
+
+    if (mode != BWD_BITS_ONLY) {
+        // phase 1: occurrence terms into shared memory, four items per thread in flight
+        const int items = nocc << gshift;
+        for (int base = threadIdx.x; base < items; base += 4 * kThreads) {
+            int o[4];
+            uint32_t wd[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int it = base + u * kThreads;
+                o[u] = it < items ? __ldg(I.occ + s0 + (it >> gshift)) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int it = base + u * kThreads;
+                wd[u] = it < items ? __ldg(ubits + (((int64_t)(o[u] >> 1) * B + col) >> 5)) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int it = base + u * kThreads;
+                if (it < items) {
+                    float term[VW];
+                    occ_term<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], wd[u], col, term);
+                    float *dst = sterm + (int64_t)(it >> gshift) * B + col;
+                    if constexpr (VW == 4) {
+                        *reinterpret_cast<float4 *>(dst) = make_float4(term[0], term[1], term[2], term[3]);
+                    } else if constexpr (VW == 2) {
+                        *reinterpret_cast<float2 *>(dst) = make_float2(term[0], term[1]);
+                    } else {
+                        dst[0] = term[0];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // phase 2: one thread per (variable, restart group)
+    const int vloc = threadIdx.x >> gshift;
+    const int i = v0 + vloc;
+    if (i >= v1) return;
+    const int64_t q0 = (int64_t)i * B + col;
+    float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
+    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
+    if (mode == BWD_BITS_ONLY) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+            if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+        return;
+    }
+    const int rb = __ldg(I.voff + i) - s0, re = __ldg(I.voff + i + 1) - s0;
+    LeafCounter<LightLevels<VW>::value> lc[VW];
+    float leaf[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
-        cs[e] = D.cscale[col + e];
-        gsc[e] = gscale ? gscale[col + e] : 1.0f;
-        upd[e] = mode == BWD_UPDATE && D.cost[col + e] != 0;
-        imp[e] = mode != BWD_GRAD_ONLY && D.improved[col + e] != 0;
+        lc[e].init();
+        leaf[e] = 0.0f;
     }
-    const long long total = (long long)I.n * G;
-    const long long stride = (long long)lblocks * blockDim.x;
-    for (long long item = (long long)lblock * blockDim.x + threadIdx.x; item < total; item += stride) {
-        const int i = (int)(item / G);
-        const int beg = __ldg(I.voff + i), end = __ldg(I.voff + i + 1);
-        if (end - beg > I.heavy_deg) continue;
-        const int64_t q0 = (int64_t)i * B + col;
-        float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-        if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(xin + q0, xv);
-        if (mode == BWD_BITS_ONLY) {
-#pragma unroll
-            for (int e = 0; e < VW; ++e)
-                if (imp[e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-            continue;
+    int in_leaf = 0;
+    for (int r = rb; r < re; ++r) {
+        float term[VW];
+        const float *src = sterm + (int64_t)r * B + col;
+        if constexpr (VW == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(src);
+            term[0] = v.x; term[1] = v.y; term[2] = v.z; term[3] = v.w;
+        } else if constexpr (VW == 2) {
+            const float2 v = *reinterpret_cast<const float2 *>(src);
+            term[0] = v.x; term[1] = v.y;
+        } else {
+            term[0] = src[0];
         }
-        float Ssum[VW];
-        occ_sum_thread<VW>(I, kfix, tcur, ubits, cs, beg, end, col, Ssum);
-        float gr[VW];
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
-            gr[e] = Ssum[e] * fmaf(-tv, tv, 1.0f);
-        }
-        if (mode == BWD_GRAD_ONLY) {
+        for (int e = 0; e < VW; ++e) leaf[e] = (in_leaf == 0) ? term[e] : leaf[e] + term[e];
+        if (++in_leaf == 32) {
 #pragma unroll
-            for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gsc[e] : gr[e];
-            stv<VW>(grad_out + q0, gr);
-            continue;
+            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+            in_leaf = 0;
         }
-        float mv[VW], vv[VW], xn[VW], tn[VW];
-        ldv_rw<VW>(S.mom + q0, mv);
-        ldv_rw<VW>(S.vel + q0, vv);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            xn[e] = upd[e] ? adam_update(A, xv[e], mv[e], vv[e], gr[e]) : xv[e];
-            if (imp[e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-            tn[e] = tanh_fixed(xn[e]);
-        }
-        stv<VW>(S.x + q0, xn);
-        stv<VW>(S.mom + q0, mv);
-        stv<VW>(S.vel + q0, vv);
-        stv<VW>(tnext + q0, tn);
     }
+    if (in_leaf) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+    }
+    float gr[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
+        gr[e] = lc[e].finish() * fmaf(-tv, tv, 1.0f);
+    }
+    if (mode == BWD_GRAD_ONLY) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gscale[col + e] : gr[e];
+        stv<VW>(grad_out + q0, gr);
+        return;
+    }
+    float mv[VW], vv[VW], xn[VW], tn[VW];
+    ldv_rw<VW>(S.mom + q0, mv);
+    ldv_rw<VW>(S.vel + q0, vv);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        xn[e] = (D.cost[col + e] != 0) ? adam_update(A, xv[e], mv[e], vv[e], gr[e]) : xv[e];
+        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+        tn[e] = tanh_fixed(xn[e]);
+    }
+    stv<VW>(S.x + q0, xn);
+    stv<VW>(S.mom + q0, mv);
+    stv<VW>(S.vel + q0, vv);
+    stv<VW>(tnext + q0, tn);
 }
 
 template <int VW, int KFIX>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
-                                     int mode, const float *x_ovr, const float *t_ovr,
-                                     const float *gscale, float *grad_out, cudaStream_t st) {
+                                     int mode, const float *t_ovr, const float *gscale,
+                                     float *grad_out, cudaStream_t st) {
     const int G = I.B / VW;
-    const long long items = (long long)I.n * G;
-    long long lblocks = (items + kThreads - 1) / kThreads;
-    if (lblocks > 152 * 8) lblocks = 152 * 8;
-    if (lblocks < 1) lblocks = 1;
-    long long hblocks = 0;
     if (I.n_heavy > 0) {
         const long long warps = I.heavy_chunks * G;  // one warp per (chunk, group)
-        hblocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
+        long long hblocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
         if (hblocks > 152 * 8) hblocks = 152 * 8;
+        k_backward_heavy<VW, KFIX><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
+                                                                            gscale, grad_out);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
     }
-    k_backward<VW, KFIX><<<(int)(hblocks + lblocks), kThreads, 0, st>>>(
-        I, S, D, mode, x_ovr, t_ovr, gscale, grad_out, (int)hblocks);
+    const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
+    const size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
+    k_backward_light<VW, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
+                                                                           gscale, grad_out);
     return cudaGetLastError();
 }
 
 template <int VW>
 static cudaError_t launch_backward_vw(const DevInst &I, const DevState &S, const DevStep &D,
-                                      int mode, const float *x_ovr, const float *t_ovr,
-                                      const float *gscale, float *grad_out, cudaStream_t st) {
-    if (I.kfix == 3)
-        return launch_backward_k<VW, 3>(I, S, D, mode, x_ovr, t_ovr, gscale, grad_out, st);
-    return launch_backward_k<VW, 0>(I, S, D, mode, x_ovr, t_ovr, gscale, grad_out, st);
+                                      int mode, const float *t_ovr, const float *gscale,
+                                      float *grad_out, cudaStream_t st) {
+    if (I.kfix == 3) return launch_backward_k<VW, 3>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    return launch_backward_k<VW, 0>(I, S, D, mode, t_ovr, gscale, grad_out, st);
 }
 
 cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
-                            const float *x_override, const float *t_override,
-                            const float *gscale, float *grad_out, cudaStream_t st) {
-    if (I.B % 4 == 0)
-        return launch_backward_vw<4>(I, S, D, mode, x_override, t_override, gscale, grad_out, st);
-    if (I.B % 2 == 0)
-        return launch_backward_vw<2>(I, S, D, mode, x_override, t_override, gscale, grad_out, st);
-    return launch_backward_vw<1>(I, S, D, mode, x_override, t_override, gscale, grad_out, st);
+                            const float *t_override, const float *gscale, float *grad_out,
+                            cudaStream_t st) {
+    if (I.B % 4 == 0) return launch_backward_vw<4>(I, S, D, mode, t_override, gscale, grad_out, st);
+    if (I.B % 2 == 0) return launch_backward_vw<2>(I, S, D, mode, t_override, gscale, grad_out, st);
+    return launch_backward_vw<1>(I, S, D, mode, t_override, gscale, grad_out, st);
 }
 
 // loss per restart from the forward partials (used where no update follows)

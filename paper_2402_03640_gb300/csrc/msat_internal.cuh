@@ -43,6 +43,9 @@ struct DevInst {
     long long heavy_chunks;       // total chunks of the heavy variables
     const int32_t *heavy_var;     // [n_heavy] variable ids
     const int32_t *heavy_chunk0;  // [n_heavy+1] prefix of chunk counts
+    int32_t n_lblk;               // blocks of the light-variable pass
+    int32_t occ_cap;              // occurrence rows one light block stages in shared memory
+    const int2 *lblk;             // [n_lblk] variable range [x, y) of each light block
 };
 
 // Scalars of the optimizer step shared by all restarts.
@@ -60,7 +63,7 @@ struct StepScalars {
 // Per-restart step state plus scratch.
 struct DevStep {
     StepScalars *sc;
-    unsigned long long *wu_acc;  // [B] atomic accumulator of sum_U w
+    unsigned long long *wu_acc;  // [kRep][B] atomic accumulators of sum_U w
     long long *cost;             // [B] cost of the evaluated x
     long long *best;             // [B] best cost so far
     int *improved;               // [B] cost < best at the last evaluation
@@ -77,12 +80,15 @@ struct DevState {
     float *t0, *t1;        // double-buffered tanh(x), [n][B]
     uint32_t *ubits;       // unsat bits, flat index j*B + b
     uint8_t *bestx;        // [n][B] best assignment (0/1)
+    float *fstore;         // [m][B] f of the last clause pass, or nullptr: recompute f
 };
 
 // Kernel modes of the variable pass.
 enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
 
 constexpr int kThreads = 256;
+constexpr int kRep = 32;                 // replicas of the per-restart cost accumulator
+constexpr int kLightSmem = 40 * 1024;    // shared memory of one light block (term rows)
 constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
 
@@ -179,8 +185,8 @@ enum { FWD_STEP = 0, FWD_EVAL = 1, FWD_PROBE = 2 };
 cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st);
 cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
-                            const float *x_override, const float *t_override,
-                            const float *gscale, float *grad_out, cudaStream_t st);
+                            const float *t_override, const float *gscale, float *grad_out,
+                            cudaStream_t st);
 cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st);
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
