@@ -278,10 +278,11 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 }
 
 // --------------------------------------------------------------- k_forward
-// One item = (clause j, restart group g).  A warp takes 64 consecutive items
-// per iteration (two per lane), so the loads of two clauses are in flight
-// together; the unsat bits of 32 consecutive items are packed with shuffles
-// into whole 32-bit words.
+// One item = (clause j, restart group g).  The grid-stride loop is unrolled
+// by two (items base + lane and base + stride + lane; the stride is a
+// multiple of G, so both belong to the thread's restart group), keeping the
+// loads of two clauses in flight; the unsat bits of 32 consecutive items are
+// packed with shuffles into whole 32-bit words.
 
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kThreads)
     const int g = threadIdx.x % G;
     const int col = g * VW;
     const long long total = (long long)I.m * G;
-    const long long stride = 2LL * gridDim.x * blockDim.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
 
     float lacc[VW];
     unsigned long long wacc[VW];
@@ -311,9 +312,9 @@ __global__ void __launch_bounds__(kThreads)
         wacc[e] = 0ull;
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
-    for (long long base = 2LL * blockIdx.x * blockDim.x + 2 * (threadIdx.x & ~31); base < total;
-         base += stride) {
-        long long item[2] = {base + lane, base + 32 + lane};
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += 2 * stride) {
+        long long item[2] = {base + lane, base + stride + lane};
         bool act[2] = {item[0] < total, item[1] < total};
         int jj[2] = {act[0] ? (int)(item[0] / G) : 0, act[1] ? (int)(item[1] / G) : 0};
         float f[2][VW];

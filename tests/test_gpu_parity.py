@@ -91,7 +91,7 @@ def test_config0_full_trajectory(pkg, oracle):
     assert got["cost_hist"][-1, 0] == ref["cost_hist"][-1, 0]
 
 
-@pytest.mark.parametrize("B", [1, 2, 4, 16, 64])
+@pytest.mark.parametrize("B", [1, 2, 4, 16, 64, 128, 256, 1024])
 def test_restarts_trajectory(pkg, oracle, B):
     cnf = uniform_ksat(300, 1290, 3, seed=5)
     check_bit_exact(oracle, cnf, B, 60, 1e-2)
