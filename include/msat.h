@@ -66,11 +66,24 @@ typedef struct {
     double beta2;     /* Adam second-moment decay (default 0.999)              */
     double eps;       /* Adam epsilon (default 1e-8)                           */
     int32_t restarts; /* B: 1, 2, 4, ..., 1024 (a power of two)                */
-    int32_t reserved0;
+    int32_t f_mode;   /* how the variable pass gets f_j of unsat clauses:
+                         MSAT_F_AUTO, MSAT_F_STORE (the clause pass stores f),
+                         MSAT_F_RECOMPUTE (recomputed from the clause CSR),
+                         MSAT_F_EXPANDED (3-literal clauses: recomputed from
+                         occurrence records holding the other two literals) */
     uint64_t seed_x;  /* seed of the random start of x (Alg. 1 line 1)         */
+    int32_t heavy_deg; /* occurrences above which a variable's sum is split
+                          into 1024-occurrence chunks (0 = automatic)          */
+    int32_t reserved1;
 } msat_config;
 
-/* Write the defaults (lr 1e-4, Adam 0.9/0.999/1e-8, B = 1, seed 1). */
+#define MSAT_F_AUTO 0
+#define MSAT_F_STORE 1
+#define MSAT_F_RECOMPUTE 2
+#define MSAT_F_EXPANDED 3
+
+/* Write the defaults (lr 1e-4, Adam 0.9/0.999/1e-8, B = 1, seed 1, automatic
+ * f mode and heavy threshold).  Every mode gives bit-identical results. */
 int msat_config_default(msat_config *cfg);
 
 /*

@@ -226,7 +226,13 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     // light blocks stage occ_cap occurrence rows of B floats in shared memory;
     // a variable with more occurrences is split into 1024-occurrence chunks
     const int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
-    const int32_t heavy_deg = occ_cap;
+    if (cfg.f_mode < MSAT_F_AUTO || cfg.f_mode > MSAT_F_EXPANDED)
+        return fail(MSAT_EINVAL, "msat_create: unknown f_mode");
+    if (cfg.f_mode == MSAT_F_EXPANDED && (kfix != 3 || m >= (1LL << 28)))
+        return fail(MSAT_EINVAL, "msat_create: MSAT_F_EXPANDED needs every clause to have 3 literals");
+    if (cfg.heavy_deg < 0) return fail(MSAT_EINVAL, "msat_create: heavy_deg < 0");
+    const int32_t heavy_deg = cfg.heavy_deg > 0 ? std::min(cfg.heavy_deg, std::min(occ_cap, kLightMaxDeg))
+                                                : std::min(occ_cap, kLightMaxDeg);
     std::vector<int32_t> hvar, hchunk0(1, 0);
     std::vector<int2> lblk;
     {
@@ -257,7 +263,26 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     }
     // f of the clause pass is kept when the [m][B] array is small; otherwise
     // the variable pass recomputes f of unsatisfied clauses
-    const bool use_fstore = (double)m * B * sizeof(float) <= 96.0 * (1 << 20) || B <= 2;
+    const bool auto_store = (double)m * B * sizeof(float) <= 96.0 * (1 << 20) || B <= 2;
+    const bool use_fstore = cfg.f_mode == MSAT_F_STORE || (cfg.f_mode == MSAT_F_AUTO && auto_store);
+    // recomputing f of 3-literal clauses reads the other two literals from an
+    // expanded occurrence record streamed with the occurrence list
+    const bool expand = cfg.f_mode == MSAT_F_EXPANDED ||
+                        (cfg.f_mode == MSAT_F_AUTO && !use_fstore && kfix == 3 && m < (1LL << 28));
+    std::vector<int2> occx;
+    if (expand) {
+        occx.resize((size_t)nnz);
+        std::vector<int32_t> fill(voff.begin(), voff.end() - 1);
+        for (int64_t j = 0; j < m; ++j)
+            for (int32_t p = 0; p < 3; ++p) {
+                const int32_t L = lit[(size_t)(3 * j + p)];
+                const int32_t slot = fill[(size_t)(L >> 1)]++;
+                occ[(size_t)slot] = (int32_t)(j << 3) | (p << 1) | (L & 1);
+                const int32_t a = lit[(size_t)(3 * j + (p == 0 ? 1 : 0))];
+                const int32_t b = lit[(size_t)(3 * j + (p == 2 ? 1 : 2))];
+                occx[(size_t)slot] = make_int2(a, b);
+            }
+    }
 
     msat_ctx *c = new (std::nothrow) msat_ctx();
     if (!c) return fail(MSAT_ENOMEM, "msat_create: host allocation failed");
@@ -277,7 +302,7 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     int rc = MSAT_OK;
     int32_t *d_coff = nullptr, *d_lit = nullptr, *d_voff = nullptr, *d_occ = nullptr;
     int32_t *d_hvar = nullptr, *d_hch = nullptr;
-    int2 *d_lblk = nullptr;
+    int2 *d_lblk = nullptr, *d_occx = nullptr;
     int64_t *d_w = nullptr;
 #define TRY_ALLOC(ptr, count)                          \
     do {                                               \
@@ -292,6 +317,7 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     TRY_ALLOC(d_hvar, (int64_t)hvar.size());
     TRY_ALLOC(d_hch, (int64_t)hchunk0.size());
     TRY_ALLOC(d_lblk, (int64_t)lblk.size());
+    if (expand) TRY_ALLOC(d_occx, nnz);
     if (use_fstore) TRY_ALLOC(c->S.fstore, m * B);
     TRY_ALLOC(c->S.x, nB);
     TRY_ALLOC(c->S.mom, nB);
@@ -316,6 +342,8 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     I.heavy_chunks = hchunk0.back();
     I.heavy_var = d_hvar;
     I.heavy_chunk0 = d_hch;
+    I.occ_shift = expand ? 3 : 1;
+    I.occx = d_occx;
     I.n_lblk = (int32_t)lblk.size();
     I.occ_cap = occ_cap;
     I.lblk = d_lblk;
@@ -363,6 +391,7 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     if (!e) e = up(d_hvar, hvar.data(), sizeof(int32_t) * hvar.size());
     if (!e) e = up(d_hch, hchunk0.data(), sizeof(int32_t) * hchunk0.size());
     if (!e) e = up(d_lblk, lblk.data(), sizeof(int2) * lblk.size());
+    if (!e && expand) e = up(d_occx, occx.data(), sizeof(int2) * occx.size());
     if (!e) e = up(D.sc, &sc, sizeof(sc));
     if (!e) e = up(D.best, best.data(), sizeof(long long) * best.size());
     if (!e) e = cudaMemsetAsync(D.wu_acc, 0, sizeof(unsigned long long) * (size_t)kRep * B, st);

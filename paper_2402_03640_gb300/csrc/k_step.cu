@@ -69,6 +69,34 @@ __device__ __forceinline__ void stv(float *p, const float (&o)[VW]) {
     }
 }
 
+// Streaming (evict-first) accesses for data touched once per pass, so the
+// gathered rows of t, the unsat bits and the f store keep their L2 lines.
+__device__ __forceinline__ int ld_stream_i32(const int *p) { return __ldcs(p); }
+
+template <int VW>
+__device__ __forceinline__ void ldv_stream(const float *p, float (&o)[VW]) {
+    if constexpr (VW == 4) {
+        float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (VW == 2) {
+        float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        o[0] = __ldcs(p);
+    }
+}
+
+template <int VW>
+__device__ __forceinline__ void stv_stream(float *p, const float (&o)[VW]) {
+    if constexpr (VW == 4) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
+    } else if constexpr (VW == 2) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(o[0], o[1]));
+    } else {
+        __stcs(p, o[0]);
+    }
+}
+
 __device__ __forceinline__ void clause_range(const DevInst &I, int kfix, int j, int &beg, int &end) {
     if (kfix > 0) {
         beg = j * kfix;
@@ -162,16 +190,21 @@ __device__ __forceinline__ void clause_value_fixed(const DevInst &I, const float
     }
 }
 
-// Occurrence term for VW restarts given the occurrence word o = j << 1 | neg
-// and the unsat word covering (j, col): +-((float)w_j * f_j) * (2/W_U) where
-// clause j is unsat, +0 elsewhere.  f comes from the clause pass's store when
-// there is one, else it is recomputed from the clause in the same order.
+// Occurrence term for VW restarts given the occurrence word o (clause j in
+// the bits above occ_shift, literal sign in bit 0) and the unsat word
+// covering (j, col): +-((float)w_j * f_j) * (2/W_U) where clause j is unsat,
+// +0 elsewhere.  f comes from the clause pass's store when there is one;
+// otherwise it is recomputed in the literal order, for 3-literal clauses from
+// the expanded occurrence record (position of the variable in bits 1-2 of o,
+// the other two literals in occx[s]; own_var is the occurring variable).
 template <int VW, int KFIX>
-__device__ __forceinline__ void occ_term(const DevInst &I, int kfix, const float *__restrict__ t,
-                                         const float *__restrict__ fstore, const float (&cs)[VW],
-                                         int o, uint32_t wd, int col, float (&term)[VW]) {
+__device__ __forceinline__ void occ_term_any(const DevInst &I, int kfix,
+                                             const float *__restrict__ t,
+                                             const float *__restrict__ fstore,
+                                             const float (&cs)[VW], int o, uint32_t wd, int col,
+                                             int own_var, int s, float (&term)[VW]) {
     const int B = I.B;
-    const int j = o >> 1;
+    const int j = o >> I.occ_shift;
     const bool neg = o & 1;
     const int64_t qb = (int64_t)j * B + col;
     const uint32_t nib = (wd >> (qb & 31)) & ((1u << VW) - 1u);
@@ -183,7 +216,30 @@ __device__ __forceinline__ void occ_term(const DevInst &I, int kfix, const float
         ldv<VW>(fstore + qb, f);
     } else {
         bool sat[VW];
-        if constexpr (KFIX > 0) {
+        if constexpr (KFIX == 3) {
+            if (I.occx) {
+                const int pos = (o >> 1) & 3;
+                const int2 ot = __ldg(I.occx + s);
+                const int own = (own_var << 1) | (o & 1);
+                int L[3];
+                L[0] = pos == 0 ? own : ot.x;
+                L[1] = pos == 0 ? ot.x : (pos == 1 ? own : ot.y);
+                L[2] = pos == 2 ? own : ot.y;
+                float tv[3][VW];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) ldv<VW>(t + (int64_t)(L[p] >> 1) * B + col, tv[p]);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) {
+                        const float tt = (L[p] & 1) ? -tv[p][e] : tv[p][e];
+                        f[e] = (p == 0) ? tt : f[e] + tt;
+                    }
+                }
+            } else {
+                clause_value_fixed<VW, 3>(I, t, j, col, f, sat);
+            }
+        } else if constexpr (KFIX > 0) {
             clause_value_fixed<VW, KFIX>(I, t, j, col, f, sat);
         } else {
             int beg, end;
@@ -227,8 +283,8 @@ __device__ __forceinline__ float adam_update(const AdamView &A, float x, float &
 
 template <int VW>
 struct LightLevels {
-    // occurrence rows of one light block / 32, rounded up to a power of two
-    static constexpr int value = VW == 1 ? 9 : (VW == 2 ? 8 : 7);
+    // a light variable has at most kLightMaxDeg occurrences: 16 leaves
+    static constexpr int value = 5;
 };
 
 }  // namespace
@@ -404,8 +460,17 @@ __global__ void __launch_bounds__(kThreads)
     if (!s_last) return;
     __threadfence();
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        // every block's additions are complete (fence before the counter):
+        // read the replicas from L2 together, then clear them for the next pass
+        unsigned long long rep[kRep];
+#pragma unroll
+        for (int r = 0; r < kRep; ++r) rep[r] = __ldcg(D.wu_acc + (long long)r * B + b);
         unsigned long long wu = 0;
-        for (int r = 0; r < kRep; ++r) wu += atomicExch(D.wu_acc + (long long)r * B + b, 0ull);
+#pragma unroll
+        for (int r = 0; r < kRep; ++r) {
+            wu += rep[r];
+            D.wu_acc[(long long)r * B + b] = 0ull;
+        }
         const long long c = (long long)wu;
         D.cost[b] = c;
         if (mode != FWD_PROBE) {
@@ -470,10 +535,51 @@ cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D
 // fixed order and applies 1 - t^2 and Adam.  Block b < B also reduces the
 // loss of restart b from the forward partials.
 
+// Update of one (variable, restart group) from its occurrence sum S: the
+// gradient S * (1 - t^2), then Adam (unless the restart has stopped), the
+// best-assignment capture and tanh of the new x; or, in the gradient-only
+// mode, the scaled gradient.  xv holds x (t in the gradient-only mode).
+template <int VW>
+__device__ __forceinline__ void finish_variable(const DevState &S, const DevStep &D,
+                                                const AdamView &A, int mode, int64_t q0,
+                                                int col, const float (&xv)[VW],
+                                                const float (&Ssum)[VW], float *tnext,
+                                                const float *__restrict__ gscale,
+                                                float *__restrict__ grad_out) {
+    float gr[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
+        gr[e] = Ssum[e] * fmaf(-tv, tv, 1.0f);
+    }
+    if (mode == BWD_GRAD_ONLY) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gscale[col + e] : gr[e];
+        stv<VW>(grad_out + q0, gr);
+        return;
+    }
+    float mv[VW], vv[VW], xn[VW], tn[VW];
+    ldv_stream<VW>(S.mom + q0, mv);
+    ldv_stream<VW>(S.vel + q0, vv);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        xn[e] = (D.cost[col + e] != 0) ? adam_update(A, xv[e], mv[e], vv[e], gr[e]) : xv[e];
+        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+        tn[e] = tanh_fixed(xn[e]);
+    }
+    stv_stream<VW>(S.x + q0, xn);
+    stv_stream<VW>(S.mom + q0, mv);
+    stv_stream<VW>(S.vel + q0, vv);
+    stv<VW>(tnext + q0, tn);
+}
+
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
     k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
                      const float *__restrict__ gscale, float *__restrict__ grad_out) {
+    // one block per (1024-occurrence chunk, restart group) of a heavy variable
+    __shared__ float s_term[kChunk * VW];
+    __shared__ int s_last;
     const int B = I.B;
     const int G = B / VW;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
@@ -486,135 +592,124 @@ __global__ void __launch_bounds__(kThreads)
     } else {
         tcur = t_ovr;
     }
-    const uint32_t *__restrict__ ubits = S.ubits;
-    const float *__restrict__ fstore = S.fstore;
-
     AdamView A;
     {
         const StepScalars *sc = D.sc;
-        A.a_t = sc->a_t;
-        A.r_t = sc->r_t;
-        A.b1 = sc->b1f;
-        A.b2 = sc->b2f;
-        A.omb1 = sc->omb1f;
-        A.omb2 = sc->omb2f;
-        A.eps = sc->epsf;
+        A.a_t = sc->a_t; A.r_t = sc->r_t; A.b1 = sc->b1f; A.b2 = sc->b2f;
+        A.omb1 = sc->omb1f; A.omb2 = sc->omb2f; A.eps = sc->epsf;
     }
-
-    {
-        // ---------------- heavy variables: one warp per (chunk, restart group)
-        const int lane = threadIdx.x & 31;
-        const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-        const long long nchunks = I.heavy_chunks;
-        for (long long it = warp; it < nchunks * G; it += nwarps) {
-            const int gg = (int)(it % G);
-            const long long cidx = it / G;
-            const int col = gg * VW;
-            int lo = 0, hi = I.n_heavy - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (__ldg(I.heavy_chunk0 + mid) <= cidx) lo = mid; else hi = mid - 1;
-            }
-            const int h = lo;
-            const int i = __ldg(I.heavy_var + h);
-            const int c0 = __ldg(I.heavy_chunk0 + h);
-            const int nch = __ldg(I.heavy_chunk0 + h + 1) - c0;
-            const int c = (int)(cidx - c0);
-            const int vbeg = __ldg(I.voff + i), vend = __ldg(I.voff + i + 1);
-            float cs[VW];
+    const int gg = blockIdx.x % G;
+    const long long cidx = blockIdx.x / G;
+    const int col = gg * VW;
+    int lo = 0, hi = I.n_heavy - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(I.heavy_chunk0 + mid) <= cidx) lo = mid; else hi = mid - 1;
+    }
+    const int h = lo;
+    const int i = __ldg(I.heavy_var + h);
+    const int c0 = __ldg(I.heavy_chunk0 + h);
+    const int nch = __ldg(I.heavy_chunk0 + h + 1) - c0;
+    const int c = (int)(cidx - c0);
+    const int vbeg = __ldg(I.voff + i), vend = __ldg(I.voff + i + 1);
+    const int cb = vbeg + c * kChunk;
+    const int cn = min(kChunk, vend - cb);  // occurrences in this chunk
+    const int lane = threadIdx.x & 31;
+    float cs[VW];
 #pragma unroll
-            for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
+    for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
+
+    if (mode != BWD_BITS_ONLY) {
+        // phase 1: the chunk's terms into shared memory, four per thread in flight
+        int o[4];
+        uint32_t wd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = threadIdx.x + u * kThreads;
+            o[u] = r < cn ? ld_stream_i32(I.occ + cb + r) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = threadIdx.x + u * kThreads;
+            wd[u] = r < cn ? __ldg(S.ubits + (((int64_t)(o[u] >> I.occ_shift) * B + col) >> 5)) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = threadIdx.x + u * kThreads;
+            if (r < cn) {
+                float term[VW];
+                occ_term_any<VW, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], wd[u], col, i, cb + r, term);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) s_term[r * VW + e] = term[e];
+            }
+        }
+        __syncthreads();
+        // phase 2: 32 leaves of 32 terms in order, then the dyadic tree
+        if (threadIdx.x < 32) {
             float leaf[VW];
 #pragma unroll
             for (int e = 0; e < VW; ++e) leaf[e] = 0.0f;
-            if (mode != BWD_BITS_ONLY) {
-                const int lb = vbeg + c * kChunk + lane * 32;
-                const int le = min(lb + 32, vend);
-                for (int s = lb; s < le; ++s) {
-                    const int o = __ldg(I.occ + s);
-                    const uint32_t wd = __ldg(ubits + (((int64_t)(o >> 1) * B + col) >> 5));
-                    float term[VW];
-                    occ_term<VW, KFIX>(I, kfix, tcur, fstore, cs, o, wd, col, term);
+            const int lb = lane * 32, le = min(lb + 32, cn);
+            for (int r = lb; r < le; ++r)
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) leaf[e] = (s == lb) ? term[e] : leaf[e] + term[e];
-                }
-                const int rem = vend - (vbeg + c * kChunk);
-                const int K = min(32, (rem + 31) / 32);
+                for (int e = 0; e < VW; ++e) leaf[e] = (r == lb) ? s_term[r * VW + e] : leaf[e] + s_term[r * VW + e];
+            const int K = (cn + 31) / 32;
 #pragma unroll
-                for (int e = 0; e < VW; ++e) leaf[e] = warp_dyadic(leaf[e], K, lane);
-                if (lane == 0) {
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) D.hpart[cidx * B + col + e] = leaf[e];
-                }
-            }
-            __threadfence();
-            unsigned prev = 0;
-            if (lane == 0) prev = atomicAdd(D.hcount + (long long)h * G + gg, 1u);
-            prev = __shfl_sync(0xffffffffu, prev, 0);
-            if (prev != (unsigned)(nch - 1)) continue;
-            __threadfence();
-            // last warp of this (variable, group): combine the chunk partials
-            LeafCounter<12> lc[VW];
-#pragma unroll
-            for (int e = 0; e < VW; ++e) lc[e].init();
-            if (mode != BWD_BITS_ONLY) {
-                for (int base = 0; base < nch; base += 32) {
-                    const int Kc = min(32, nch - base);
-                    float v[VW];
-#pragma unroll
-                    for (int e = 0; e < VW; ++e)
-                        v[e] = (lane < Kc) ? __ldcg(D.hpart + (c0 + base + lane) * (long long)B + col + e)
-                                           : 0.0f;
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        v[e] = warp_dyadic(v[e], Kc, lane);
-                        lc[e].push(v[e]);
-                    }
-                }
-            }
+            for (int e = 0; e < VW; ++e) leaf[e] = warp_dyadic(leaf[e], K, lane);
             if (lane == 0) {
-                D.hcount[(long long)h * G + gg] = 0;
-                const int64_t q0 = (int64_t)i * B + col;
-                float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-                if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
-                if (mode == BWD_BITS_ONLY) {
 #pragma unroll
-                    for (int e = 0; e < VW; ++e)
-                        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-                } else {
-                    float gr[VW];
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
-                        gr[e] = lc[e].finish() * fmaf(-tv, tv, 1.0f);
-                    }
-                    if (mode == BWD_GRAD_ONLY) {
-#pragma unroll
-                        for (int e = 0; e < VW; ++e)
-                            grad_out[q0 + e] = gscale ? gr[e] * gscale[col + e] : gr[e];
-                    } else {
-                        float mv[VW], vv[VW], xn[VW], tn[VW];
-                        ldv_rw<VW>(S.mom + q0, mv);
-                        ldv_rw<VW>(S.vel + q0, vv);
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) {
-                            xn[e] = xv[e];
-                            if (D.cost[col + e] != 0) xn[e] = adam_update(A, xv[e], mv[e], vv[e], gr[e]);
-                            if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-                            tn[e] = tanh_fixed(xn[e]);
-                        }
-                        stv<VW>(S.x + q0, xn);
-                        stv<VW>(S.mom + q0, mv);
-                        stv<VW>(S.vel + q0, vv);
-                        stv<VW>(tnext + q0, tn);
-                    }
-                }
+                for (int e = 0; e < VW; ++e) D.hpart[cidx * B + col + e] = leaf[e];
             }
         }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = (atomicAdd(D.hcount + (long long)h * G + gg, 1u) == (unsigned)(nch - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last chunk block of this (variable, group): dyadic tree over the chunk
+    // partials, kChunk of them per round (a round is a complete dyadic block)
+    LeafCounter<8> lc[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) lc[e].init();
+    if (mode != BWD_BITS_ONLY) {
+        for (int base = 0; base < nch; base += kChunk) {
+            const int K = min(kChunk, nch - base);
+            __syncthreads();
+            for (int r = threadIdx.x; r < K; r += kThreads)
+#pragma unroll
+                for (int e = 0; e < VW; ++e)
+                    s_term[r * VW + e] = __ldcg(D.hpart + (long long)(c0 + base + r) * B + col + e);
+            __syncthreads();
+            for (int st = 1; st < K; st <<= 1) {
+                for (int r = threadIdx.x * 2 * st; r < K; r += kThreads * 2 * st)
+                    if (r + st < K)
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) s_term[r * VW + e] = s_term[r * VW + e] + s_term[(r + st) * VW + e];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0)
+#pragma unroll
+                for (int e = 0; e < VW; ++e) lc[e].push(s_term[e]);
+        }
+    }
+    if (threadIdx.x != 0) return;
+    D.hcount[(long long)h * G + gg] = 0;
+    const int64_t q0 = (int64_t)i * B + col;
+    float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
+    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
+    if (mode == BWD_BITS_ONLY) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+            if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
         return;
     }
-
+    float Ssum[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) Ssum[e] = lc[e].finish();
+    finish_variable<VW>(S, D, A, mode, q0, col, xv, Ssum, tnext, gscale, grad_out);
 }
 
 template <int VW, int KFIX>
@@ -671,12 +766,16 @@ __global__ void __launch_bounds__(kThreads)
     }
 
     // ------------------------------------------------------- light block
+    __shared__ int s_voff[kThreads + 1];
     float *sterm = reinterpret_cast<float *>(dyn_smem);
     if ((int)blockIdx.x >= I.n_lblk) return;  // a grid of one block when every variable is heavy
     const int2 rg = I.lblk[blockIdx.x];
     const int v0 = rg.x, v1 = rg.y;
-    const int s0 = __ldg(I.voff + v0);
-    const int nocc = __ldg(I.voff + v1) - s0;
+    const int nv = v1 - v0;
+    for (int r = threadIdx.x; r <= nv; r += kThreads) s_voff[r] = __ldg(I.voff + v0 + r);
+    __syncthreads();
+    const int s0 = s_voff[0];
+    const int nocc = s_voff[nv] - s0;
     const int gshift = __ffs(G) - 1;  // G is a power of two
     const int g = threadIdx.x & (G - 1);
     const int col = g * VW;
@@ -693,20 +792,31 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
-                o[u] = it < items ? __ldg(I.occ + s0 + (it >> gshift)) : 0;
+                o[u] = it < items ? ld_stream_i32(I.occ + s0 + (it >> gshift)) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
-                wd[u] = it < items ? __ldg(ubits + (((int64_t)(o[u] >> 1) * B + col) >> 5)) : 0u;
+                wd[u] = it < items ? __ldg(ubits + (((int64_t)(o[u] >> I.occ_shift) * B + col) >> 5)) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
                 if (it < items) {
+                    const int r = it >> gshift;
+                    int own = 0;
+                    if (KFIX == 3 && I.occx) {
+                        // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
+                        int lo = 0, hi = nv - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
+                        }
+                        own = v0 + lo;
+                    }
                     float term[VW];
-                    occ_term<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], wd[u], col, term);
-                    float *dst = sterm + (int64_t)(it >> gshift) * B + col;
+                    occ_term_any<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], wd[u], col, own, s0 + r, term);
+                    float *dst = sterm + (int64_t)r * B + col;
                     if constexpr (VW == 4) {
                         *reinterpret_cast<float4 *>(dst) = make_float4(term[0], term[1], term[2], term[3]);
                     } else if constexpr (VW == 2) {
@@ -722,18 +832,18 @@ __global__ void __launch_bounds__(kThreads)
 
     // phase 2: one thread per (variable, restart group)
     const int vloc = threadIdx.x >> gshift;
+    if (vloc >= nv) return;
     const int i = v0 + vloc;
-    if (i >= v1) return;
     const int64_t q0 = (int64_t)i * B + col;
     float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
+    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_stream<VW>(S.x + q0, xv);
     if (mode == BWD_BITS_ONLY) {
 #pragma unroll
         for (int e = 0; e < VW; ++e)
             if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
         return;
     }
-    const int rb = __ldg(I.voff + i) - s0, re = __ldg(I.voff + i + 1) - s0;
+    const int rb = s_voff[vloc] - s0, re = s_voff[vloc + 1] - s0;
     LeafCounter<LightLevels<VW>::value> lc[VW];
     float leaf[VW];
 #pragma unroll
@@ -766,31 +876,10 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
     }
-    float gr[VW];
+    float Ssum[VW];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
-        gr[e] = lc[e].finish() * fmaf(-tv, tv, 1.0f);
-    }
-    if (mode == BWD_GRAD_ONLY) {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gscale[col + e] : gr[e];
-        stv<VW>(grad_out + q0, gr);
-        return;
-    }
-    float mv[VW], vv[VW], xn[VW], tn[VW];
-    ldv_rw<VW>(S.mom + q0, mv);
-    ldv_rw<VW>(S.vel + q0, vv);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        xn[e] = (D.cost[col + e] != 0) ? adam_update(A, xv[e], mv[e], vv[e], gr[e]) : xv[e];
-        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-        tn[e] = tanh_fixed(xn[e]);
-    }
-    stv<VW>(S.x + q0, xn);
-    stv<VW>(S.mom + q0, mv);
-    stv<VW>(S.vel + q0, vv);
-    stv<VW>(tnext + q0, tn);
+    for (int e = 0; e < VW; ++e) Ssum[e] = lc[e].finish();
+    finish_variable<VW>(S, D, A, mode, q0, col, xv, Ssum, tnext, gscale, grad_out);
 }
 
 template <int VW, int KFIX>
@@ -799,9 +888,7 @@ static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const 
                                      float *grad_out, cudaStream_t st) {
     const int G = I.B / VW;
     if (I.n_heavy > 0) {
-        const long long warps = I.heavy_chunks * G;  // one warp per (chunk, group)
-        long long hblocks = (warps + (kThreads / 32) - 1) / (kThreads / 32);
-        if (hblocks > 152 * 8) hblocks = 152 * 8;
+        const long long hblocks = I.heavy_chunks * G;  // one block per (chunk, group)
         k_backward_heavy<VW, KFIX><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
                                                                             gscale, grad_out);
         cudaError_t e = cudaGetLastError();

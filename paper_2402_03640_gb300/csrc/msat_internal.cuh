@@ -43,6 +43,9 @@ struct DevInst {
     long long heavy_chunks;       // total chunks of the heavy variables
     const int32_t *heavy_var;     // [n_heavy] variable ids
     const int32_t *heavy_chunk0;  // [n_heavy+1] prefix of chunk counts
+    int32_t occ_shift;            // occ word: clause index above this bit (1, or 3 when
+                                  // bits 1-2 hold the variable's position in its clause)
+    const int2 *occx;             // [nnz] other two literals of a 3-literal clause, or nullptr
     int32_t n_lblk;               // blocks of the light-variable pass
     int32_t occ_cap;              // occurrence rows one light block stages in shared memory
     const int2 *lblk;             // [n_lblk] variable range [x, y) of each light block
@@ -89,6 +92,7 @@ enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
 constexpr int kThreads = 256;
 constexpr int kRep = 32;                 // replicas of the per-restart cost accumulator
 constexpr int kLightSmem = 40 * 1024;    // shared memory of one light block (term rows)
+constexpr int kLightMaxDeg = 512;        // more occurrences than this: heavy variable
 constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
 

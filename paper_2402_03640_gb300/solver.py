@@ -48,7 +48,7 @@ class Solver:
 
     def __init__(self, n: int, off, lits, weights=None, restarts: int = 1, seed_x: int = 1,
                  lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-                 stream=None):
+                 stream=None, f_mode: str = "auto", heavy_deg: int = 0):
         lib = native.load()
         self._lib = lib
         cfg = native.msat_config()
@@ -56,6 +56,8 @@ class Solver:
         cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
         cfg.restarts = int(restarts)
         cfg.seed_x = int(seed_x)
+        cfg.f_mode = native.F_MODES[f_mode]
+        cfg.heavy_deg = int(heavy_deg)
         off = np.ascontiguousarray(off, dtype=np.int64)
         lits = np.ascontiguousarray(lits, dtype=np.int32)
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)

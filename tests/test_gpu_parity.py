@@ -25,10 +25,10 @@ def pkg():
     return p
 
 
-def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1):
+def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, **kw):
     """Cost after each evaluation (x_0 .. x_steps), loss of each update, final x."""
     costs, losses = [], []
-    with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=seed_x, lr=lr) as s:
+    with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=seed_x, lr=lr, **kw) as s:
         costs.append(s.step(0, want_loss=False)[1])
         done = 0
         while done < steps:
@@ -44,9 +44,9 @@ def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1):
                 best_cost=best, info=info)
 
 
-def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, loss_every=1):
+def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, **kw):
     ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr)
-    got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk)
+    got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk, **kw)
     idx = [0] + [min(k, steps) for k in range(chunk, steps + chunk, chunk)] if steps else [0]
     want_costs = ref["cost_hist"][idx]
     assert np.array_equal(got["cost_hist"], want_costs), "unsat cost history differs"
@@ -95,6 +95,24 @@ def test_config0_full_trajectory(pkg, oracle):
 def test_restarts_trajectory(pkg, oracle, B):
     cnf = uniform_ksat(300, 1290, 3, seed=5)
     check_bit_exact(oracle, cnf, B, 60, 1e-2)
+
+
+@pytest.mark.parametrize("f_mode", ["store", "recompute", "expanded"])
+@pytest.mark.parametrize("B", [1, 4, 16, 256])
+def test_f_modes_identical(pkg, oracle, f_mode, B):
+    """Every way of getting f_j to the variable pass gives the same bits."""
+    cnf = uniform_ksat(700, 3010, 3, seed=9)
+    check_bit_exact(oracle, cnf, B, 12, 2e-2, f_mode=f_mode)
+
+
+@pytest.mark.parametrize("heavy_deg", [1, 8, 40])
+@pytest.mark.parametrize("f_mode", ["store", "recompute"])
+def test_heavy_split_identical(pkg, oracle, heavy_deg, f_mode):
+    """Forcing variables into the chunked heavy path keeps every bit."""
+    cnf = zipf_weighted(1500, 6000, seed=2)
+    check_bit_exact(oracle, cnf, 2, 8, 2e-2, f_mode=f_mode, heavy_deg=heavy_deg)
+    cnf3 = uniform_ksat(400, 1720, 3, seed=4)
+    check_bit_exact(oracle, cnf3, 16, 8, 2e-2, f_mode="expanded", heavy_deg=heavy_deg)
 
 
 def test_larger_lr_chunked_steps(pkg, oracle):
