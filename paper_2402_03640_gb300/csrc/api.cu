@@ -147,6 +147,8 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     if (!clause_off) return fail(MSAT_EINVAL, "msat_create: clause_off is NULL");
     if (!valid_restarts(cfg.restarts))
         return fail(MSAT_EINVAL, "msat_create: restarts must be a power of two in [1, 1024]");
+    if (n_clauses * (int64_t)cfg.restarts >= (1LL << 31) || (int64_t)n_vars * cfg.restarts >= (1LL << 31))
+        return fail(MSAT_EINVAL, "msat_create: m * restarts and n * restarts must stay below 2^31");
     if (!(cfg.lr > 0) || !(cfg.beta1 >= 0 && cfg.beta1 < 1) || !(cfg.beta2 >= 0 && cfg.beta2 < 1) ||
         !(cfg.eps >= 0))
         return fail(MSAT_EINVAL, "msat_create: Adam settings out of range");

@@ -190,30 +190,39 @@ __device__ __forceinline__ void clause_value_fixed(const DevInst &I, const float
     }
 }
 
-// Occurrence term for VW restarts given the occurrence word o (clause j in
-// the bits above occ_shift, literal sign in bit 0) and the unsat word
-// covering (j, col): +-((float)w_j * f_j) * (2/W_U) where clause j is unsat,
-// +0 elsewhere.  f comes from the clause pass's store when there is one;
-// otherwise it is recomputed in the literal order, for 3-literal clauses from
-// the expanded occurrence record (position of the variable in bits 1-2 of o,
-// the other two literals in occx[s]; own_var is the occurring variable).
+// Unsat bits of (clause of occurrence word o, restarts col .. col+VW-1)
+// from the 32-bit word wd that holds them (flat bit index j*B + col, which
+// fits 32 bits: the context rejects m*B >= 2^31).
+template <int VW>
+__device__ __forceinline__ uint32_t occ_nib(const DevInst &I, int o, uint32_t wd, int col) {
+    const uint32_t qb = (uint32_t)(o >> I.occ_shift) * (uint32_t)I.B + (uint32_t)col;
+    return (wd >> (qb & 31u)) & ((1u << VW) - 1u);
+}
+
+__device__ __forceinline__ const uint32_t *ubits_word(const DevInst &I, const uint32_t *ubits,
+                                                      int o, int col) {
+    return ubits + (((uint32_t)(o >> I.occ_shift) * (uint32_t)I.B + (uint32_t)col) >> 5);
+}
+
+// Occurrence term for VW restarts of occurrence word o (clause j in the bits
+// above occ_shift, literal sign in bit 0) whose unsat bits nib are not all
+// zero: +-((float)w_j * f_j) * (2/W_U) where clause j is unsat, +0
+// elsewhere.  f comes from the clause pass's store when there is one;
+// otherwise it is recomputed in the literal order, for 3-literal clauses
+// from the expanded occurrence record (position of the variable in bits 1-2
+// of o, the other two literals in occx[s]; own_var is the occurring variable).
 template <int VW, int KFIX>
-__device__ __forceinline__ void occ_term_any(const DevInst &I, int kfix,
-                                             const float *__restrict__ t,
-                                             const float *__restrict__ fstore,
-                                             const float (&cs)[VW], int o, uint32_t wd, int col,
-                                             int own_var, int s, float (&term)[VW]) {
+__device__ __forceinline__ void occ_term_unsat(const DevInst &I, int kfix,
+                                               const float *__restrict__ t,
+                                               const float *__restrict__ fstore,
+                                               const float (&cs)[VW], int o, uint32_t nib, int col,
+                                               int own_var, int s, float (&term)[VW]) {
     const int B = I.B;
     const int j = o >> I.occ_shift;
     const bool neg = o & 1;
-    const int64_t qb = (int64_t)j * B + col;
-    const uint32_t nib = (wd >> (qb & 31)) & ((1u << VW) - 1u);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) term[e] = 0.0f;
-    if (!nib) return;
     float f[VW];
     if (fstore) {
-        ldv<VW>(fstore + qb, f);
+        ldv<VW>(fstore + (int64_t)j * B + col, f);
     } else {
         bool sat[VW];
         if constexpr (KFIX == 3) {
@@ -250,6 +259,7 @@ __device__ __forceinline__ void occ_term_any(const DevInst &I, int kfix,
     const float wj = I.w ? (float)__ldg(I.w + j) : 1.0f;
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
+        term[e] = 0.0f;
         if ((nib >> e) & 1u) {
             const float g = (wj * f[e]) * cs[e];
             term[e] = neg ? -g : g;
@@ -631,14 +641,17 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
-            wd[u] = r < cn ? __ldg(S.ubits + (((int64_t)(o[u] >> I.occ_shift) * B + col) >> 5)) : 0u;
+            wd[u] = r < cn ? __ldg(ubits_word(I, S.ubits, o[u], col)) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
             if (r < cn) {
                 float term[VW];
-                occ_term_any<VW, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], wd[u], col, i, cb + r, term);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) term[e] = 0.0f;
+                const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
+                if (nib) occ_term_unsat<VW, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], nib, col, i, cb + r, term);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) s_term[r * VW + e] = term[e];
             }
@@ -797,25 +810,30 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
-                wd[u] = it < items ? __ldg(ubits + (((int64_t)(o[u] >> I.occ_shift) * B + col) >> 5)) : 0u;
+                wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], col)) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
                 if (it < items) {
                     const int r = it >> gshift;
-                    int own = 0;
-                    if (KFIX == 3 && I.occx) {
-                        // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
-                        int lo = 0, hi = nv - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
-                        }
-                        own = v0 + lo;
-                    }
                     float term[VW];
-                    occ_term_any<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], wd[u], col, own, s0 + r, term);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) term[e] = 0.0f;
+                    const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
+                    if (nib) {
+                        int own = 0;
+                        if (KFIX == 3 && I.occx) {
+                            // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
+                            int lo = 0, hi = nv - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
+                            }
+                            own = v0 + lo;
+                        }
+                        occ_term_unsat<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], nib, col, own, s0 + r, term);
+                    }
                     float *dst = sterm + (int64_t)r * B + col;
                     if constexpr (VW == 4) {
                         *reinterpret_cast<float4 *>(dst) = make_float4(term[0], term[1], term[2], term[3]);
