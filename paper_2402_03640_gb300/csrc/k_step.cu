@@ -1,19 +1,22 @@
 // Step kernels of the MaxSAT gradient engine (sm_103a).
 //
-//   k_init      random start of x (Alg. 1 line 1), zero Adam moments, tanh(x)
-//   k_forward   clause pass: f_j, exact unsat bits, sum_U w and the loss
-//               partials per restart; the last block to finish turns them
-//               into cost, best, 2/W_U and the Adam step scalars
-//   k_backward  variable pass over the transposed CSR: occurrence sum of
-//               +-dL/df_j, times 1 - t^2, fused Adam update, best-assignment
-//               capture and tanh of the new x.  Variables with more than
-//               heavy_deg occurrences are split into 1024-occurrence chunks
-//               handled by whole warps and combined in the fixed tree order.
+//   k_init            random start of x (Alg. 1 line 1), zero Adam moments,
+//                     tanh(x)
+//   k_forward         clause pass: f_j, exact unsat bits, sum_U w and the
+//                     loss partials per restart; the last block to finish
+//                     turns them into cost, best, 2/W_U and the Adam scalars
+//   k_backward_light  variable pass over the transposed CSR for variables
+//                     with few occurrences: occurrence terms staged in shared
+//                     memory, then per variable the fixed-order sum, 1 - t^2,
+//                     fused Adam update, best-assignment capture and tanh
+//   k_backward_heavy  the same for variables with many occurrences, split
+//                     into 1024-occurrence chunks combined in the fixed order
 //
 // Layouts: x, mom, vel, t are float [n][B] (restart index innermost), so the
-// B values of one variable are one contiguous, vector-loadable row.  Each
-// thread owns VW consecutive restarts (VW = 4, 2 or 1) of one clause or
-// variable.
+// B values of one variable are one contiguous, vector-loadable row.  A
+// thread owns VW consecutive restarts of one clause, occurrence or variable:
+// up to 8 in the clause pass, up to 16 when staging occurrence terms, up to
+// 4 in the update (where every restart carries x, m, v, t and the sums).
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,27 +34,38 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
     return z ^ (z >> 31);
 }
 
+// --------------------------------------------------------- vector access
+// VW floats at p (16-byte aligned for VW >= 4): read-only (nc) loads,
+// coherent loads, streaming (evict-first) loads and stores.  Streaming is
+// used for data touched once per pass, so the gathered rows of t, the unsat
+// bits and the f store keep their L2 lines.
+
 template <int VW>
 __device__ __forceinline__ void ldv(const float *__restrict__ p, float (&o)[VW]) {
-    if constexpr (VW == 4) {
-        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    if constexpr (VW >= 4) {
+#pragma unroll
+        for (int k = 0; k < VW / 4; ++k) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
+            o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+        }
     } else if constexpr (VW == 2) {
-        float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
         o[0] = v.x; o[1] = v.y;
     } else {
         o[0] = __ldg(p);
     }
 }
 
-// plain (coherent) vector load, for arrays this kernel also writes
 template <int VW>
 __device__ __forceinline__ void ldv_rw(const float *p, float (&o)[VW]) {
-    if constexpr (VW == 4) {
-        float4 v = *reinterpret_cast<const float4 *>(p);
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    if constexpr (VW >= 4) {
+#pragma unroll
+        for (int k = 0; k < VW / 4; ++k) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[k];
+            o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+        }
     } else if constexpr (VW == 2) {
-        float2 v = *reinterpret_cast<const float2 *>(p);
+        const float2 v = *reinterpret_cast<const float2 *>(p);
         o[0] = v.x; o[1] = v.y;
     } else {
         o[0] = *p;
@@ -59,27 +73,15 @@ __device__ __forceinline__ void ldv_rw(const float *p, float (&o)[VW]) {
 }
 
 template <int VW>
-__device__ __forceinline__ void stv(float *p, const float (&o)[VW]) {
-    if constexpr (VW == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    } else if constexpr (VW == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
-    } else {
-        *p = o[0];
-    }
-}
-
-// Streaming (evict-first) accesses for data touched once per pass, so the
-// gathered rows of t, the unsat bits and the f store keep their L2 lines.
-__device__ __forceinline__ int ld_stream_i32(const int *p) { return __ldcs(p); }
-
-template <int VW>
 __device__ __forceinline__ void ldv_stream(const float *p, float (&o)[VW]) {
-    if constexpr (VW == 4) {
-        float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    if constexpr (VW >= 4) {
+#pragma unroll
+        for (int k = 0; k < VW / 4; ++k) {
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(p) + k);
+            o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+        }
     } else if constexpr (VW == 2) {
-        float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+        const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
         o[0] = v.x; o[1] = v.y;
     } else {
         o[0] = __ldcs(p);
@@ -87,15 +89,32 @@ __device__ __forceinline__ void ldv_stream(const float *p, float (&o)[VW]) {
 }
 
 template <int VW>
+__device__ __forceinline__ void stv(float *p, const float (&o)[VW]) {
+    if constexpr (VW >= 4) {
+#pragma unroll
+        for (int k = 0; k < VW / 4; ++k)
+            reinterpret_cast<float4 *>(p)[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+    } else if constexpr (VW == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+    } else {
+        *p = o[0];
+    }
+}
+
+template <int VW>
 __device__ __forceinline__ void stv_stream(float *p, const float (&o)[VW]) {
-    if constexpr (VW == 4) {
-        __stcs(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
+    if constexpr (VW >= 4) {
+#pragma unroll
+        for (int k = 0; k < VW / 4; ++k)
+            __stcs(reinterpret_cast<float4 *>(p) + k, make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]));
     } else if constexpr (VW == 2) {
         __stcs(reinterpret_cast<float2 *>(p), make_float2(o[0], o[1]));
     } else {
         __stcs(p, o[0]);
     }
 }
+
+// ------------------------------------------------------------ clause sums
 
 __device__ __forceinline__ void clause_range(const DevInst &I, int kfix, int j, int &beg, int &end) {
     if (kfix > 0) {
@@ -121,13 +140,13 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
     }
     if (end - beg <= 32) {
         for (int p = beg; p < end; ++p) {
-            int L = __ldg(I.lit + p);
-            bool neg = L & 1;
+            const int L = __ldg(I.lit + p);
+            const bool neg = L & 1;
             float tv[VW];
             ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                float term = neg ? -tv[e] : tv[e];
+                const float term = neg ? -tv[e] : tv[e];
                 f[e] = (p == beg) ? term : f[e] + term;
                 if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
             }
@@ -139,13 +158,13 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
         for (int e = 0; e < VW; ++e) lc[e].init();
         int in_leaf = 0;
         for (int p = beg; p < end; ++p) {
-            int L = __ldg(I.lit + p);
-            bool neg = L & 1;
+            const int L = __ldg(I.lit + p);
+            const bool neg = L & 1;
             float tv[VW];
             ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                float term = neg ? -tv[e] : tv[e];
+                const float term = neg ? -tv[e] : tv[e];
                 leaf[e] = (in_leaf == 0) ? term : leaf[e] + term;
                 if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
             }
@@ -190,13 +209,16 @@ __device__ __forceinline__ void clause_value_fixed(const DevInst &I, const float
     }
 }
 
+// ------------------------------------------------------- occurrence terms
+
 // Unsat bits of (clause of occurrence word o, restarts col .. col+VW-1)
 // from the 32-bit word wd that holds them (flat bit index j*B + col, which
 // fits 32 bits: the context rejects m*B >= 2^31).
 template <int VW>
 __device__ __forceinline__ uint32_t occ_nib(const DevInst &I, int o, uint32_t wd, int col) {
     const uint32_t qb = (uint32_t)(o >> I.occ_shift) * (uint32_t)I.B + (uint32_t)col;
-    return (wd >> (qb & 31u)) & ((1u << VW) - 1u);
+    constexpr uint32_t mask = VW >= 32 ? 0xffffffffu : ((1u << VW) - 1u);
+    return (wd >> (qb & 31u)) & mask;
 }
 
 __device__ __forceinline__ const uint32_t *ubits_word(const DevInst &I, const uint32_t *ubits,
@@ -271,31 +293,93 @@ __device__ __forceinline__ void occ_term_unsat(const DevInst &I, int kfix,
 __device__ __forceinline__ float warp_dyadic(float v, int K, int lane) {
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
-        float o = __shfl_down_sync(0xffffffffu, v, s);
+        const float o = __shfl_down_sync(0xffffffffu, v, s);
         if ((lane & (2 * s - 1)) == 0 && lane + s < K) v = v + o;
     }
     return v;
 }
 
+// --------------------------------------------------------------- update
+
 struct AdamView {
     float a_t, r_t, b1, b2, omb1, omb2, eps;
 };
 
+__device__ __forceinline__ AdamView adam_view(const StepScalars *sc) {
+    AdamView A;
+    A.a_t = sc->a_t;
+    A.r_t = sc->r_t;
+    A.b1 = sc->b1f;
+    A.b2 = sc->b2f;
+    A.omb1 = sc->omb1f;
+    A.omb2 = sc->omb2f;
+    A.eps = sc->epsf;
+    return A;
+}
+
 __device__ __forceinline__ float adam_update(const AdamView &A, float x, float &m, float &v,
                                              float g) {
-    float mq = A.b1 * m + A.omb1 * g;
-    float vq = A.b2 * v + (A.omb2 * g) * g;
-    float den = sqrtf(vq) * A.r_t + A.eps;
+    const float mq = A.b1 * m + A.omb1 * g;
+    const float vq = A.b2 * v + (A.omb2 * g) * g;
+    const float den = sqrtf(vq) * A.r_t + A.eps;
     m = mq;
     v = vq;
     return x - (A.a_t * mq) / den;
 }
 
+// Update of one (variable, restart group) from its occurrence sum S: the
+// gradient S * (1 - t^2) with t = tanh(x) of the evaluated x, then Adam
+// (unless the restart has stopped), the best-assignment capture and tanh of
+// the new x; or, in the gradient-only mode, the scaled gradient.
 template <int VW>
-struct LightLevels {
-    // a light variable has at most kLightMaxDeg occurrences: 16 leaves
-    static constexpr int value = 5;
-};
+__device__ __forceinline__ void finish_variable(const DevState &S, const DevStep &D,
+                                                const AdamView &A, int mode, int64_t q0,
+                                                int col, const float *__restrict__ tcur,
+                                                const float (&Ssum)[VW], float *tnext,
+                                                const float *__restrict__ gscale,
+                                                float *__restrict__ grad_out) {
+    float tv[VW], gr[VW];
+    ldv<VW>(tcur + q0, tv);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) gr[e] = Ssum[e] * fmaf(-tv[e], tv[e], 1.0f);
+    if (mode == BWD_GRAD_ONLY) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gscale[col + e] : gr[e];
+        stv<VW>(grad_out + q0, gr);
+        return;
+    }
+    float xv[VW], mv[VW], vv[VW], tn[VW];
+    ldv_stream<VW>(S.x + q0, xv);
+    ldv_stream<VW>(S.mom + q0, mv);
+    ldv_stream<VW>(S.vel + q0, vv);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+        if (D.cost[col + e] != 0) {
+            xv[e] = adam_update(A, xv[e], mv[e], vv[e], gr[e]);
+            tn[e] = tanh_fixed(xv[e]);
+        } else {
+            tn[e] = tv[e];
+        }
+    }
+    stv_stream<VW>(S.x + q0, xv);
+    stv_stream<VW>(S.mom + q0, mv);
+    stv_stream<VW>(S.vel + q0, vv);
+    stv<VW>(tnext + q0, tn);
+}
+
+__device__ __forceinline__ void step_buffers(const DevState &S, const DevStep &D, int mode,
+                                             const float *t_ovr, const float *&tcur,
+                                             float *&tnext) {
+    const long long steps = D.sc->steps_done;
+    if (mode == BWD_UPDATE) {
+        tcur = ((steps - 1) & 1) ? S.t1 : S.t0;
+        tnext = (steps & 1) ? S.t1 : S.t0;
+    } else {
+        tcur = t_ovr ? t_ovr : ((steps & 1) ? S.t1 : S.t0);
+        tnext = nullptr;
+    }
+}
 
 }  // namespace
 
@@ -307,11 +391,11 @@ __global__ void k_init(int n, int B, uint64_t seed, float *__restrict__ x,
     const int64_t total = (int64_t)n * B;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q / B;
-        int64_t b = q - i * B;
-        uint64_t u = splitmix64_at(seed, (uint64_t)b * (uint64_t)n + (uint64_t)i);
-        float k = (float)(uint32_t)(u >> 40);
-        float xv = k * 0x1p-23f - 1.0f;
+        const int64_t i = q / B;
+        const int64_t b = q - i * B;
+        const uint64_t u = splitmix64_at(seed, (uint64_t)b * (uint64_t)n + (uint64_t)i);
+        const float k = (float)(uint32_t)(u >> 40);
+        const float xv = k * 0x1p-23f - 1.0f;
         x[q] = xv;
         mom[q] = 0.0f;
         vel[q] = 0.0f;
@@ -321,7 +405,7 @@ __global__ void k_init(int n, int B, uint64_t seed, float *__restrict__ x,
 }
 
 cudaError_t launch_init(const DevInst &I, const DevState &S, uint64_t seed, cudaStream_t st) {
-    int64_t total = (int64_t)I.n * I.B;
+    const int64_t total = (int64_t)I.n * I.B;
     int blocks = (int)((total + kThreads - 1) / kThreads);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
@@ -344,19 +428,21 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 }
 
 // --------------------------------------------------------------- k_forward
-// One item = (clause j, restart group g).  The grid-stride loop is unrolled
-// by two (items base + lane and base + stride + lane; the stride is a
-// multiple of G, so both belong to the thread's restart group), keeping the
-// loads of two clauses in flight; the unsat bits of 32 consecutive items are
-// packed with shuffles into whole 32-bit words.
+// One item = (clause j, restart group g of VW restarts).  For VW <= 4 the
+// grid-stride loop is unrolled by two (items base + lane and base + stride +
+// lane; the stride is a multiple of G, so both belong to the thread's
+// restart group), keeping the loads of two clauses in flight; wider groups
+// already have VW/4 row loads per literal in flight.  The unsat bits of 32
+// consecutive items are packed with shuffles into whole 32-bit words.
 
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
     k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
               const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
               float *__restrict__ fstore, int mode) {
-    __shared__ unsigned long long s_w[kThreads * VW];
-    __shared__ float s_l[kThreads * VW];
+    constexpr int NU = VW <= 4 ? 2 : 1;  // items per lane per iteration
+    __shared__ unsigned long long s_w[kThreads];
+    __shared__ float s_l[kThreads];
     __shared__ int s_last;
 
     const int B = I.B;
@@ -379,27 +465,33 @@ __global__ void __launch_bounds__(kThreads)
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += 2 * stride) {
-        long long item[2] = {base + lane, base + stride + lane};
-        bool act[2] = {item[0] < total, item[1] < total};
-        int jj[2] = {act[0] ? (int)(item[0] / G) : 0, act[1] ? (int)(item[1] / G) : 0};
-        float f[2][VW];
-        bool sat[2][VW];
-        if constexpr (KFIX > 0) {
-            // both clauses' literals, then both clauses' rows
-            int L[2][KFIX];
+         base += NU * stride) {
+        long long item[NU];
+        bool act[NU];
+        int jj[NU];
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < NU; ++h) {
+            item[h] = base + h * stride + lane;
+            act[h] = item[h] < total;
+            jj[h] = act[h] ? (int)(item[h] / G) : 0;
+        }
+        float f[NU][VW];
+        bool sat[NU][VW];
+        if constexpr (KFIX > 0) {
+            // every clause's literals, then every clause's rows
+            int L[NU][KFIX];
+#pragma unroll
+            for (int h = 0; h < NU; ++h)
 #pragma unroll
                 for (int p = 0; p < KFIX; ++p) L[h][p] = __ldg(I.lit + jj[h] * KFIX + p);
-            float tv[2][KFIX][VW];
+            float tv[NU][KFIX][VW];
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < NU; ++h)
 #pragma unroll
                 for (int p = 0; p < KFIX; ++p)
                     ldv<VW>(t + (int64_t)(L[h][p] >> 1) * B + col, tv[h][p]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < NU; ++h)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     sat[h][e] = false;
@@ -413,14 +505,14 @@ __global__ void __launch_bounds__(kThreads)
                 }
         } else {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < NU; ++h) {
                 int beg = 0, end = 0;
                 if (act[h]) clause_range(I, kfix, jj[h], beg, end);
                 clause_value<VW, true>(I, t, beg, end, col, f[h], sat[h]);
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < NU; ++h) {
             unsigned nib = 0;
             if (act[h]) {
                 const long long wj = I.w ? __ldg(I.w + jj[h]) : 1ll;
@@ -442,45 +534,39 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
 
+    // per restart: block sums (one restart slot of the group at a time)
+    unsigned long long *acc = D.wu_acc + (long long)(blockIdx.x % kRep) * B;
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
-        s_w[threadIdx.x * VW + e] = wacc[e];
-        s_l[threadIdx.x * VW + e] = lacc[e];
-    }
-    __syncthreads();
-    if (threadIdx.x < G) {
-        unsigned long long *acc = D.wu_acc + (long long)(blockIdx.x % kRep) * B;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
+        s_w[threadIdx.x] = wacc[e];
+        s_l[threadIdx.x] = lacc[e];
+        __syncthreads();
+        if (threadIdx.x < G) {
             unsigned long long sw = 0;
             float sl = 0.0f;
             for (int r = threadIdx.x; r < blockDim.x; r += G) {
-                sw += s_w[r * VW + e];
-                sl += s_l[r * VW + e];
+                sw += s_w[r];
+                sl += s_l[r];
             }
             const int b = threadIdx.x * VW + e;
             if (sw) atomicAdd(acc + b, sw);
             D.lpart[(long long)blockIdx.x * B + b] = sl;
         }
+        __syncthreads();
     }
     __threadfence();
-    __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(&D.sc->counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         // every block's additions are complete (fence before the counter):
-        // read the replicas from L2 together, then clear them for the next pass
-        unsigned long long rep[kRep];
-#pragma unroll
-        for (int r = 0; r < kRep; ++r) rep[r] = __ldcg(D.wu_acc + (long long)r * B + b);
+        // read the replicas from L2, then clear them for the next pass
         unsigned long long wu = 0;
-#pragma unroll
-        for (int r = 0; r < kRep; ++r) {
-            wu += rep[r];
-            D.wu_acc[(long long)r * B + b] = 0ull;
-        }
+#pragma unroll 8
+        for (int r = 0; r < kRep; ++r) wu += __ldcg(D.wu_acc + (long long)r * B + b);
+#pragma unroll 8
+        for (int r = 0; r < kRep; ++r) D.wu_acc[(long long)r * B + b] = 0ull;
         const long long c = (long long)wu;
         D.cost[b] = c;
         if (mode != FWD_PROBE) {
@@ -506,10 +592,14 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+static int vw_forward(int B) { return B < 8 ? B : 8; }
+static int vw_stage(int B) { return B < 16 ? B : 16; }
+
 int fwd_grid_blocks(const DevInst &I) {
-    const int VW = (I.B % 4 == 0) ? 4 : (I.B % 2 == 0 ? 2 : 1);
+    const int VW = vw_forward(I.B);
+    const int per_thread = VW <= 4 ? 2 : 1;
     const long long items = (long long)I.m * (I.B / VW);
-    long long blocks = (items + 2 * kThreads - 1) / (2 * kThreads);
+    long long blocks = (items + per_thread * kThreads - 1) / (per_thread * kThreads);
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
@@ -528,86 +618,56 @@ static cudaError_t launch_forward_vw(const DevInst &I, const DevState &S, const 
 
 cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st) {
-    if (I.B % 4 == 0) return launch_forward_vw<4>(I, S, D, mode, t_override, st);
-    if (I.B % 2 == 0) return launch_forward_vw<2>(I, S, D, mode, t_override, st);
-    return launch_forward_vw<1>(I, S, D, mode, t_override, st);
+    switch (vw_forward(I.B)) {
+        case 8: return launch_forward_vw<8>(I, S, D, mode, t_override, st);
+        case 4: return launch_forward_vw<4>(I, S, D, mode, t_override, st);
+        case 2: return launch_forward_vw<2>(I, S, D, mode, t_override, st);
+        default: return launch_forward_vw<1>(I, S, D, mode, t_override, st);
+    }
 }
 
 // -------------------------------------------------------------- k_backward
-// k_backward_heavy: variables with more occurrences than a light block can
-// stage, one warp per (1024-occurrence chunk, restart group); the last warp
-// of a (variable, group) combines the chunk partials in the fixed tree order
-// and applies the update.
-// k_backward_light: one block per range of consecutive light variables.
-// Phase 1 spreads the block's (occurrence, restart group) items over all
-// threads and stages each occurrence term in shared memory; phase 2 gives
-// each (variable, restart group) to one thread, which sums its terms in the
-// fixed order and applies 1 - t^2 and Adam.  Block b < B also reduces the
-// loss of restart b from the forward partials.
+// Per restart b < B, block b of the light kernel also reduces the loss of
+// the evaluated x from the forward block partials.
 
-// Update of one (variable, restart group) from its occurrence sum S: the
-// gradient S * (1 - t^2), then Adam (unless the restart has stopped), the
-// best-assignment capture and tanh of the new x; or, in the gradient-only
-// mode, the scaled gradient.  xv holds x (t in the gradient-only mode).
-template <int VW>
-__device__ __forceinline__ void finish_variable(const DevState &S, const DevStep &D,
-                                                const AdamView &A, int mode, int64_t q0,
-                                                int col, const float (&xv)[VW],
-                                                const float (&Ssum)[VW], float *tnext,
-                                                const float *__restrict__ gscale,
-                                                float *__restrict__ grad_out) {
-    float gr[VW];
-#pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        const float tv = (mode == BWD_GRAD_ONLY) ? xv[e] : tanh_fixed(xv[e]);
-        gr[e] = Ssum[e] * fmaf(-tv, tv, 1.0f);
+__device__ __forceinline__ void reduce_loss(const DevStep &D, int B) {
+    __shared__ float s_red[kThreads];
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+        float acc = 0.0f;
+        for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
+            acc += D.lpart[(long long)k * B + b];
+        s_red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const long long c = D.cost[b];
+            D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
+        }
+        __syncthreads();
     }
-    if (mode == BWD_GRAD_ONLY) {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) gr[e] = gscale ? gr[e] * gscale[col + e] : gr[e];
-        stv<VW>(grad_out + q0, gr);
-        return;
-    }
-    float mv[VW], vv[VW], xn[VW], tn[VW];
-    ldv_stream<VW>(S.mom + q0, mv);
-    ldv_stream<VW>(S.vel + q0, vv);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        xn[e] = (D.cost[col + e] != 0) ? adam_update(A, xv[e], mv[e], vv[e], gr[e]) : xv[e];
-        if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-        tn[e] = tanh_fixed(xn[e]);
-    }
-    stv_stream<VW>(S.x + q0, xn);
-    stv_stream<VW>(S.mom + q0, mv);
-    stv_stream<VW>(S.vel + q0, vv);
-    stv<VW>(tnext + q0, tn);
 }
 
+// k_backward_heavy: one block per (1024-occurrence chunk, restart group of
+// VW restarts) of a heavy variable.  The chunk's terms are staged in shared
+// memory; 32 leaves of 32 terms are summed in order and combined by the
+// dyadic tree; the last chunk block of a (variable, group) combines the
+// chunk partials with the same tree and applies the update.
 template <int VW, int KFIX>
 __global__ void __launch_bounds__(kThreads)
     k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
                      const float *__restrict__ gscale, float *__restrict__ grad_out) {
-    // one block per (1024-occurrence chunk, restart group) of a heavy variable
     __shared__ float s_term[kChunk * VW];
     __shared__ int s_last;
     const int B = I.B;
     const int G = B / VW;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
-    const long long steps = D.sc->steps_done;
     const float *tcur;
-    float *tnext = nullptr;
-    if (mode == BWD_UPDATE) {
-        tcur = ((steps - 1) & 1) ? S.t1 : S.t0;
-        tnext = (steps & 1) ? S.t1 : S.t0;
-    } else {
-        tcur = t_ovr;
-    }
-    AdamView A;
-    {
-        const StepScalars *sc = D.sc;
-        A.a_t = sc->a_t; A.r_t = sc->r_t; A.b1 = sc->b1f; A.b2 = sc->b2f;
-        A.omb1 = sc->omb1f; A.omb2 = sc->omb2f; A.eps = sc->epsf;
-    }
+    float *tnext;
+    step_buffers(S, D, mode, t_ovr, tcur, tnext);
+    const AdamView A = adam_view(D.sc);
     const int gg = blockIdx.x % G;
     const long long cidx = blockIdx.x / G;
     const int col = gg * VW;
@@ -636,7 +696,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
-            o[u] = r < cn ? ld_stream_i32(I.occ + cb + r) : 0;
+            o[u] = r < cn ? __ldcs(I.occ + cb + r) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -711,9 +771,9 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x != 0) return;
     D.hcount[(long long)h * G + gg] = 0;
     const int64_t q0 = (int64_t)i * B + col;
-    float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_rw<VW>(S.x + q0, xv);
     if (mode == BWD_BITS_ONLY) {
+        float xv[VW];
+        ldv_rw<VW>(S.x + q0, xv);
 #pragma unroll
         for (int e = 0; e < VW; ++e)
             if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
@@ -722,66 +782,31 @@ __global__ void __launch_bounds__(kThreads)
     float Ssum[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) Ssum[e] = lc[e].finish();
-    finish_variable<VW>(S, D, A, mode, q0, col, xv, Ssum, tnext, gscale, grad_out);
+    finish_variable<VW>(S, D, A, mode, q0, col, tcur, Ssum, tnext, gscale, grad_out);
 }
 
-template <int VW, int KFIX>
+// k_backward_light: one block per range of consecutive light variables.
+// Phase 1 spreads the block's (occurrence, group of VS restarts) items over
+// all threads and stages each occurrence term in shared memory (row r of
+// the block's occurrences, B floats); phase 2 gives each (variable, group of
+// VU restarts) to one thread, which sums its rows in the fixed order and
+// applies the update.
+template <int VS, int VU, int KFIX>
 __global__ void __launch_bounds__(kThreads)
     k_backward_light(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
                      const float *__restrict__ gscale, float *__restrict__ grad_out) {
     extern __shared__ float4 dyn_smem[];
-    const int B = I.B;
-    const int G = B / VW;
-    const int kfix = KFIX > 0 ? KFIX : I.kfix;
-    const long long steps = D.sc->steps_done;
-    const float *tcur;
-    float *tnext = nullptr;
-    if (mode == BWD_UPDATE) {
-        tcur = ((steps - 1) & 1) ? S.t1 : S.t0;
-        tnext = (steps & 1) ? S.t1 : S.t0;
-    } else {
-        tcur = t_ovr;
-    }
-    const uint32_t *__restrict__ ubits = S.ubits;
-    const float *__restrict__ fstore = S.fstore;
-
-    // loss of the evaluated x per restart, from the forward block partials
-    if (mode == BWD_UPDATE) {
-        __shared__ float s_red[kThreads];
-        for (int b = blockIdx.x; b < B; b += gridDim.x) {
-            float acc = 0.0f;
-            for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
-                acc += D.lpart[(long long)k * B + b];
-            s_red[threadIdx.x] = acc;
-            __syncthreads();
-            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-                if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                const long long c = D.cost[b];
-                D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
-            }
-            __syncthreads();
-        }
-    }
-
-    AdamView A;
-    {
-        const StepScalars *sc = D.sc;
-        A.a_t = sc->a_t;
-        A.r_t = sc->r_t;
-        A.b1 = sc->b1f;
-        A.b2 = sc->b2f;
-        A.omb1 = sc->omb1f;
-        A.omb2 = sc->omb2f;
-        A.eps = sc->epsf;
-    }
-
-    // ------------------------------------------------------- light block
     __shared__ int s_voff[kThreads + 1];
-    float *sterm = reinterpret_cast<float *>(dyn_smem);
+    const int B = I.B;
+    const int kfix = KFIX > 0 ? KFIX : I.kfix;
+    const float *tcur;
+    float *tnext;
+    step_buffers(S, D, mode, t_ovr, tcur, tnext);
+    if (mode == BWD_UPDATE) reduce_loss(D, B);
     if ((int)blockIdx.x >= I.n_lblk) return;  // a grid of one block when every variable is heavy
+    const AdamView A = adam_view(D.sc);
+    const uint32_t *__restrict__ ubits = S.ubits;
+    float *sterm = reinterpret_cast<float *>(dyn_smem);
     const int2 rg = I.lblk[blockIdx.x];
     const int v0 = rg.x, v1 = rg.y;
     const int nv = v1 - v0;
@@ -789,38 +814,38 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     const int s0 = s_voff[0];
     const int nocc = s_voff[nv] - s0;
-    const int gshift = __ffs(G) - 1;  // G is a power of two
-    const int g = threadIdx.x & (G - 1);
-    const int col = g * VW;
-    float cs[VW];
-#pragma unroll
-    for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
 
     if (mode != BWD_BITS_ONLY) {
         // phase 1: occurrence terms into shared memory, four items per thread in flight
-        const int items = nocc << gshift;
+        const int GS = B / VS;
+        const int sshift = __ffs(GS) - 1;  // GS is a power of two
+        const int colS = (threadIdx.x & (GS - 1)) * VS;
+        float cs[VS];
+#pragma unroll
+        for (int e = 0; e < VS; ++e) cs[e] = D.cscale[colS + e];
+        const int items = nocc << sshift;
         for (int base = threadIdx.x; base < items; base += 4 * kThreads) {
             int o[4];
             uint32_t wd[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
-                o[u] = it < items ? ld_stream_i32(I.occ + s0 + (it >> gshift)) : 0;
+                o[u] = it < items ? __ldcs(I.occ + s0 + (it >> sshift)) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
-                wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], col)) : 0u;
+                wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], colS)) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int it = base + u * kThreads;
                 if (it < items) {
-                    const int r = it >> gshift;
-                    float term[VW];
+                    const int r = it >> sshift;
+                    float term[VS];
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) term[e] = 0.0f;
-                    const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
+                    for (int e = 0; e < VS; ++e) term[e] = 0.0f;
+                    const uint32_t nib = occ_nib<VS>(I, o[u], wd[u], colS);
                     if (nib) {
                         int own = 0;
                         if (KFIX == 3 && I.occx) {
@@ -832,16 +857,9 @@ __global__ void __launch_bounds__(kThreads)
                             }
                             own = v0 + lo;
                         }
-                        occ_term_unsat<VW, KFIX>(I, kfix, tcur, fstore, cs, o[u], nib, col, own, s0 + r, term);
+                        occ_term_unsat<VS, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], nib, colS, own, s0 + r, term);
                     }
-                    float *dst = sterm + (int64_t)r * B + col;
-                    if constexpr (VW == 4) {
-                        *reinterpret_cast<float4 *>(dst) = make_float4(term[0], term[1], term[2], term[3]);
-                    } else if constexpr (VW == 2) {
-                        *reinterpret_cast<float2 *>(dst) = make_float2(term[0], term[1]);
-                    } else {
-                        dst[0] = term[0];
-                    }
+                    stv<VS>(sterm + (int64_t)r * B + colS, term);
                 }
             }
         }
@@ -849,115 +867,94 @@ __global__ void __launch_bounds__(kThreads)
     }
 
     // phase 2: one thread per (variable, restart group)
-    const int vloc = threadIdx.x >> gshift;
+    const int GU = B / VU;
+    const int ushift = __ffs(GU) - 1;
+    const int colU = (threadIdx.x & (GU - 1)) * VU;
+    const int vloc = threadIdx.x >> ushift;
     if (vloc >= nv) return;
     const int i = v0 + vloc;
-    const int64_t q0 = (int64_t)i * B + col;
-    float xv[VW];  // x, or t = tanh(x) in the gradient-only mode
-    if (mode == BWD_GRAD_ONLY) ldv<VW>(tcur + q0, xv); else ldv_stream<VW>(S.x + q0, xv);
+    const int64_t q0 = (int64_t)i * B + colU;
     if (mode == BWD_BITS_ONLY) {
+        float xv[VU];
+        ldv_rw<VU>(S.x + q0, xv);
 #pragma unroll
-        for (int e = 0; e < VW; ++e)
-            if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+        for (int e = 0; e < VU; ++e)
+            if (D.improved[colU + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
         return;
     }
     const int rb = s_voff[vloc] - s0, re = s_voff[vloc + 1] - s0;
-    LeafCounter<LightLevels<VW>::value> lc[VW];
-    float leaf[VW];
+    LeafCounter<5> lc[VU];  // at most kLightMaxDeg = 512 rows: 16 leaves
+    float leaf[VU];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
+    for (int e = 0; e < VU; ++e) {
         lc[e].init();
         leaf[e] = 0.0f;
     }
     int in_leaf = 0;
     for (int r = rb; r < re; ++r) {
-        float term[VW];
-        const float *src = sterm + (int64_t)r * B + col;
-        if constexpr (VW == 4) {
-            const float4 v = *reinterpret_cast<const float4 *>(src);
-            term[0] = v.x; term[1] = v.y; term[2] = v.z; term[3] = v.w;
-        } else if constexpr (VW == 2) {
-            const float2 v = *reinterpret_cast<const float2 *>(src);
-            term[0] = v.x; term[1] = v.y;
-        } else {
-            term[0] = src[0];
-        }
+        float term[VU];
+        ldv_rw<VU>(sterm + (int64_t)r * B + colU, term);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) leaf[e] = (in_leaf == 0) ? term[e] : leaf[e] + term[e];
+        for (int e = 0; e < VU; ++e) leaf[e] = (in_leaf == 0) ? term[e] : leaf[e] + term[e];
         if (++in_leaf == 32) {
 #pragma unroll
-            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+            for (int e = 0; e < VU; ++e) lc[e].push(leaf[e]);
             in_leaf = 0;
         }
     }
     if (in_leaf) {
 #pragma unroll
-        for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+        for (int e = 0; e < VU; ++e) lc[e].push(leaf[e]);
     }
-    float Ssum[VW];
+    float Ssum[VU];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) Ssum[e] = lc[e].finish();
-    finish_variable<VW>(S, D, A, mode, q0, col, xv, Ssum, tnext, gscale, grad_out);
+    for (int e = 0; e < VU; ++e) Ssum[e] = lc[e].finish();
+    finish_variable<VU>(S, D, A, mode, q0, colU, tcur, Ssum, tnext, gscale, grad_out);
 }
 
-template <int VW, int KFIX>
+template <int VS, int VU, int KFIX>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
                                      int mode, const float *t_ovr, const float *gscale,
                                      float *grad_out, cudaStream_t st) {
-    const int G = I.B / VW;
     if (I.n_heavy > 0) {
-        const long long hblocks = I.heavy_chunks * G;  // one block per (chunk, group)
-        k_backward_heavy<VW, KFIX><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
+        const long long hblocks = I.heavy_chunks * (I.B / VU);  // one block per (chunk, group)
+        k_backward_heavy<VU, KFIX><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
                                                                             gscale, grad_out);
-        cudaError_t e = cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
         if (e) return e;
     }
     const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
     const size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
-    k_backward_light<VW, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
-                                                                           gscale, grad_out);
+    k_backward_light<VS, VU, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
+                                                                               gscale, grad_out);
     return cudaGetLastError();
 }
 
-template <int VW>
+template <int VS, int VU>
 static cudaError_t launch_backward_vw(const DevInst &I, const DevState &S, const DevStep &D,
                                       int mode, const float *t_ovr, const float *gscale,
                                       float *grad_out, cudaStream_t st) {
-    if (I.kfix == 3) return launch_backward_k<VW, 3>(I, S, D, mode, t_ovr, gscale, grad_out, st);
-    return launch_backward_k<VW, 0>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    if (I.kfix == 3) return launch_backward_k<VS, VU, 3>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    return launch_backward_k<VS, VU, 0>(I, S, D, mode, t_ovr, gscale, grad_out, st);
 }
 
 cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                             const float *t_override, const float *gscale, float *grad_out,
                             cudaStream_t st) {
-    if (I.B % 4 == 0) return launch_backward_vw<4>(I, S, D, mode, t_override, gscale, grad_out, st);
-    if (I.B % 2 == 0) return launch_backward_vw<2>(I, S, D, mode, t_override, gscale, grad_out, st);
-    return launch_backward_vw<1>(I, S, D, mode, t_override, gscale, grad_out, st);
-}
-
-// loss per restart from the forward partials (used where no update follows)
-__global__ void k_loss_reduce(DevStep D, int B) {
-    __shared__ float s_red[kThreads];
-    for (int b = blockIdx.x; b < B; b += gridDim.x) {
-        float acc = 0.0f;
-        for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
-            acc += D.lpart[(long long)k * B + b];
-        s_red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) s_red[threadIdx.x] += s_red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const long long c = D.cost[b];
-            D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
-        }
-        __syncthreads();
+    switch (vw_stage(I.B)) {
+        case 16: return launch_backward_vw<16, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 8: return launch_backward_vw<8, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 4: return launch_backward_vw<4, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 2: return launch_backward_vw<2, 2>(I, S, D, mode, t_override, gscale, grad_out, st);
+        default: return launch_backward_vw<1, 1>(I, S, D, mode, t_override, gscale, grad_out, st);
     }
 }
 
+// loss per restart from the forward partials (used where no update follows)
+__global__ void k_loss_reduce(DevStep D, int B) { reduce_loss(D, B); }
+
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st) {
-    int blocks = B < 152 * 4 ? B : 152 * 4;
+    const int blocks = B < 152 * 4 ? B : 152 * 4;
     k_loss_reduce<<<blocks, kThreads, 0, st>>>(D, B);
     return cudaGetLastError();
 }
