@@ -74,6 +74,14 @@ typedef struct {
     uint64_t seed_x;  /* seed of the random start of x (Alg. 1 line 1)         */
     int32_t heavy_deg; /* occurrences above which a variable's sum is split
                           into 1024-occurrence chunks (0 = automatic)          */
+    /* Launch shapes (0 = automatic).  None of them changes a result bit: the
+     * order of every sum is fixed by the instance, not by the launch.       */
+    int32_t fwd_vw;     /* restarts per thread in the clause pass (1,2,4,8; <= B) */
+    int32_t stage_vw;   /* restarts per thread staging occurrence terms
+                           (1,2,4,8,16; <= B)                                   */
+    int32_t fwd_blocks; /* thread blocks of the clause pass                    */
+    int32_t light_rows; /* occurrence rows a light block stages in shared
+                           memory (>= 16)                                       */
     int32_t reserved1;
 } msat_config;
 

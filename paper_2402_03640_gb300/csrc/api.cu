@@ -225,9 +225,18 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     const int32_t B = cfg.restarts;
     const int VW = (B % 4 == 0) ? 4 : (B % 2 == 0 ? 2 : 1);
     const int G = B / VW;
+    // launch shapes
+    auto pow2_le = [](int32_t v, int32_t cap) { return v >= 1 && v <= cap && (v & (v - 1)) == 0; };
+    const int32_t fwd_vw = cfg.fwd_vw ? cfg.fwd_vw : auto_fwd_vw(B);
+    const int32_t stage_vw = cfg.stage_vw ? cfg.stage_vw : auto_stage_vw(B);
+    if (!pow2_le(fwd_vw, std::min(8, B)) || !pow2_le(stage_vw, std::min(16, B)))
+        return fail(MSAT_EINVAL, "msat_create: fwd_vw / stage_vw must be powers of two <= min(8 or 16, B)");
+    if (cfg.fwd_blocks < 0 || cfg.light_rows < 0 || (cfg.light_rows > 0 && cfg.light_rows < 16))
+        return fail(MSAT_EINVAL, "msat_create: fwd_blocks >= 0 and light_rows 0 or >= 16");
     // light blocks stage occ_cap occurrence rows of B floats in shared memory;
     // a variable with more occurrences is split into 1024-occurrence chunks
-    const int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
+    int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
+    if (cfg.light_rows > 0) occ_cap = std::min(occ_cap, cfg.light_rows);
     if (cfg.f_mode < MSAT_F_AUTO || cfg.f_mode > MSAT_F_EXPANDED)
         return fail(MSAT_EINVAL, "msat_create: unknown f_mode");
     if (cfg.f_mode == MSAT_F_EXPANDED && (kfix != 3 || m >= (1LL << 28)))
@@ -348,10 +357,12 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     I.occx = d_occx;
     I.n_lblk = (int32_t)lblk.size();
     I.occ_cap = occ_cap;
+    I.fwd_vw = fwd_vw;
+    I.stage_vw = stage_vw;
     I.lblk = d_lblk;
 
     DevStep &D = c->D;
-    D.fwd_blocks = fwd_grid_blocks(I);
+    D.fwd_blocks = cfg.fwd_blocks > 0 ? cfg.fwd_blocks : fwd_grid_blocks(I);
     TRY_ALLOC(D.sc, 1);
     TRY_ALLOC(D.wu_acc, (int64_t)kRep * B);
     TRY_ALLOC(D.cost, B);

@@ -592,11 +592,12 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-static int vw_forward(int B) { return B < 8 ? B : 8; }
-static int vw_stage(int B) { return B < 16 ? B : 16; }
+int auto_fwd_vw(int B) { return B < 8 ? B : 8; }
+int auto_stage_vw(int B) { return B < 16 ? B : 16; }
+int update_vw(int B) { return B < 4 ? B : 4; }
 
 int fwd_grid_blocks(const DevInst &I) {
-    const int VW = vw_forward(I.B);
+    const int VW = I.fwd_vw;
     const int per_thread = VW <= 4 ? 2 : 1;
     const long long items = (long long)I.m * (I.B / VW);
     long long blocks = (items + per_thread * kThreads - 1) / (per_thread * kThreads);
@@ -618,7 +619,7 @@ static cudaError_t launch_forward_vw(const DevInst &I, const DevState &S, const 
 
 cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st) {
-    switch (vw_forward(I.B)) {
+    switch (I.fwd_vw) {
         case 8: return launch_forward_vw<8>(I, S, D, mode, t_override, st);
         case 4: return launch_forward_vw<4>(I, S, D, mode, t_override, st);
         case 2: return launch_forward_vw<2>(I, S, D, mode, t_override, st);
@@ -824,21 +825,24 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int e = 0; e < VS; ++e) cs[e] = D.cscale[colS + e];
         const int items = nocc << sshift;
-        for (int base = threadIdx.x; base < items; base += 4 * kThreads) {
-            int o[4];
-            uint32_t wd[4];
+        // narrow groups take four items per thread in flight; wide groups
+        // already issue VS/4 row loads per literal
+        constexpr int NB = VS <= 4 ? 4 : 1;
+        for (int base = threadIdx.x; base < items; base += NB * kThreads) {
+            int o[NB];
+            uint32_t wd[NB];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < NB; ++u) {
                 const int it = base + u * kThreads;
                 o[u] = it < items ? __ldcs(I.occ + s0 + (it >> sshift)) : 0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < NB; ++u) {
                 const int it = base + u * kThreads;
                 wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], colS)) : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < NB; ++u) {
                 const int it = base + u * kThreads;
                 if (it < items) {
                     const int r = it >> sshift;
@@ -941,12 +945,17 @@ static cudaError_t launch_backward_vw(const DevInst &I, const DevState &S, const
 cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                             const float *t_override, const float *gscale, float *grad_out,
                             cudaStream_t st) {
-    switch (vw_stage(I.B)) {
-        case 16: return launch_backward_vw<16, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
-        case 8: return launch_backward_vw<8, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
-        case 4: return launch_backward_vw<4, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
-        case 2: return launch_backward_vw<2, 2>(I, S, D, mode, t_override, gscale, grad_out, st);
-        default: return launch_backward_vw<1, 1>(I, S, D, mode, t_override, gscale, grad_out, st);
+    const int vu = update_vw(I.B);
+    switch (I.stage_vw * 8 + vu) {
+        case 16 * 8 + 4: return launch_backward_vw<16, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 8 * 8 + 4: return launch_backward_vw<8, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 4 * 8 + 4: return launch_backward_vw<4, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 2 * 8 + 4: return launch_backward_vw<2, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 1 * 8 + 4: return launch_backward_vw<1, 4>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 2 * 8 + 2: return launch_backward_vw<2, 2>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 1 * 8 + 2: return launch_backward_vw<1, 2>(I, S, D, mode, t_override, gscale, grad_out, st);
+        case 1 * 8 + 1: return launch_backward_vw<1, 1>(I, S, D, mode, t_override, gscale, grad_out, st);
+        default: return cudaErrorInvalidValue;
     }
 }
 

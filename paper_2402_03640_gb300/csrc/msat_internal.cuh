@@ -48,6 +48,8 @@ struct DevInst {
     const int2 *occx;             // [nnz] other two literals of a 3-literal clause, or nullptr
     int32_t n_lblk;               // blocks of the light-variable pass
     int32_t occ_cap;              // occurrence rows one light block stages in shared memory
+    int32_t fwd_vw;               // restarts per thread in the clause pass
+    int32_t stage_vw;             // restarts per thread staging occurrence terms
     const int2 *lblk;             // [n_lblk] variable range [x, y) of each light block
 };
 
@@ -185,6 +187,9 @@ struct LeafCounter {
 
 cudaError_t launch_init(const DevInst &I, const DevState &S, uint64_t seed, cudaStream_t st);
 int fwd_grid_blocks(const DevInst &I);
+int auto_fwd_vw(int B);
+int auto_stage_vw(int B);
+int update_vw(int B);
 enum { FWD_STEP = 0, FWD_EVAL = 1, FWD_PROBE = 2 };
 cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st);

@@ -39,7 +39,9 @@ class msat_config(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("restarts", ctypes.c_int32),
                 ("f_mode", ctypes.c_int32), ("seed_x", ctypes.c_uint64),
-                ("heavy_deg", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("heavy_deg", ctypes.c_int32), ("fwd_vw", ctypes.c_int32),
+                ("stage_vw", ctypes.c_int32), ("fwd_blocks", ctypes.c_int32),
+                ("light_rows", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 F_MODES = {"auto": 0, "store": 1, "recompute": 2, "expanded": 3}

@@ -48,7 +48,8 @@ class Solver:
 
     def __init__(self, n: int, off, lits, weights=None, restarts: int = 1, seed_x: int = 1,
                  lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-                 stream=None, f_mode: str = "auto", heavy_deg: int = 0):
+                 stream=None, f_mode: str = "auto", heavy_deg: int = 0, fwd_vw: int = 0,
+                 stage_vw: int = 0, fwd_blocks: int = 0, light_rows: int = 0):
         lib = native.load()
         self._lib = lib
         cfg = native.msat_config()
@@ -58,6 +59,8 @@ class Solver:
         cfg.seed_x = int(seed_x)
         cfg.f_mode = native.F_MODES[f_mode]
         cfg.heavy_deg = int(heavy_deg)
+        cfg.fwd_vw, cfg.stage_vw = int(fwd_vw), int(stage_vw)
+        cfg.fwd_blocks, cfg.light_rows = int(fwd_blocks), int(light_rows)
         off = np.ascontiguousarray(off, dtype=np.int64)
         lits = np.ascontiguousarray(lits, dtype=np.int32)
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)

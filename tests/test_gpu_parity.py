@@ -115,6 +115,18 @@ def test_heavy_split_identical(pkg, oracle, heavy_deg, f_mode):
     check_bit_exact(oracle, cnf3, 16, 8, 2e-2, f_mode="expanded", heavy_deg=heavy_deg)
 
 
+@pytest.mark.parametrize("shape", [
+    dict(fwd_vw=1, stage_vw=1), dict(fwd_vw=2, stage_vw=16), dict(fwd_vw=8, stage_vw=4),
+    dict(fwd_vw=4, stage_vw=8, fwd_blocks=7, light_rows=16), dict(fwd_blocks=1, light_rows=40),
+])
+def test_launch_shapes_identical(pkg, oracle, shape):
+    """Launch shapes the tuner may pick never change a bit of the result."""
+    cnf = uniform_ksat(900, 3870, 3, seed=12)
+    check_bit_exact(oracle, cnf, 16, 10, 2e-2, **shape)
+    z = zipf_weighted(1200, 5000, seed=5)
+    check_bit_exact(oracle, z, 8, 6, 2e-2, **{k: v for k, v in shape.items()})
+
+
 def test_larger_lr_chunked_steps(pkg, oracle):
     cnf = uniform_ksat(1000, 4300, 3, seed=2)
     check_bit_exact(oracle, cnf, 4, 40, 3e-2, chunk=7)
