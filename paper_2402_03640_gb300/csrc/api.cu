@@ -394,6 +394,8 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     sc.omb1f = (float)(1.0 - cfg.beta1);
     sc.omb2f = (float)(1.0 - cfg.beta2);
     sc.epsf = (float)cfg.eps;
+    sc.dense = 1;
+    sc.wsum = wsum;
     std::vector<long long> best((size_t)B, (long long)wsum);
     cudaError_t e = cudaSuccess;
     if (!e) e = up(d_coff, coff.data(), sizeof(int32_t) * coff.size());

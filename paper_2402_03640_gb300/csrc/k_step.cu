@@ -226,58 +226,62 @@ __device__ __forceinline__ const uint32_t *ubits_word(const DevInst &I, const ui
     return ubits + (((uint32_t)(o >> I.occ_shift) * (uint32_t)I.B + (uint32_t)col) >> 5);
 }
 
-// Occurrence term for VW restarts of occurrence word o (clause j in the bits
-// above occ_shift, literal sign in bit 0) whose unsat bits nib are not all
-// zero: +-((float)w_j * f_j) * (2/W_U) where clause j is unsat, +0
-// elsewhere.  f comes from the clause pass's store when there is one;
-// otherwise it is recomputed in the literal order, for 3-literal clauses
-// from the expanded occurrence record (position of the variable in bits 1-2
-// of o, the other two literals in occx[s]; own_var is the occurring variable).
+// f_j for VW restarts (col .. col+VW-1) of the clause of occurrence word o
+// (clause j in the bits above occ_shift, literal sign in bit 0).  f comes
+// from the clause pass's store when there is one; otherwise it is
+// recomputed in the literal order, for 3-literal clauses from the expanded
+// occurrence record (position of the variable in bits 1-2 of o, the other
+// two literals in ox; own_var is the occurring variable).
 template <int VW, int KFIX>
-__device__ __forceinline__ void occ_term_unsat(const DevInst &I, int kfix,
-                                               const float *__restrict__ t,
-                                               const float *__restrict__ fstore,
-                                               const float (&cs)[VW], int o, uint32_t nib, int col,
-                                               int own_var, int s, float (&term)[VW]) {
+__device__ __forceinline__ void fetch_f(const DevInst &I, int kfix, const float *__restrict__ t,
+                                        const float *__restrict__ fstore, int o, int2 ox,
+                                        int own_var, int col, float (&f)[VW]) {
     const int B = I.B;
     const int j = o >> I.occ_shift;
-    const bool neg = o & 1;
-    float f[VW];
     if (fstore) {
         ldv<VW>(fstore + (int64_t)j * B + col, f);
-    } else {
-        bool sat[VW];
-        if constexpr (KFIX == 3) {
-            if (I.occx) {
-                const int pos = (o >> 1) & 3;
-                const int2 ot = __ldg(I.occx + s);
-                const int own = (own_var << 1) | (o & 1);
-                int L[3];
-                L[0] = pos == 0 ? own : ot.x;
-                L[1] = pos == 0 ? ot.x : (pos == 1 ? own : ot.y);
-                L[2] = pos == 2 ? own : ot.y;
-                float tv[3][VW];
-#pragma unroll
-                for (int p = 0; p < 3; ++p) ldv<VW>(t + (int64_t)(L[p] >> 1) * B + col, tv[p]);
-#pragma unroll
-                for (int e = 0; e < VW; ++e) {
-#pragma unroll
-                    for (int p = 0; p < 3; ++p) {
-                        const float tt = (L[p] & 1) ? -tv[p][e] : tv[p][e];
-                        f[e] = (p == 0) ? tt : f[e] + tt;
-                    }
-                }
-            } else {
-                clause_value_fixed<VW, 3>(I, t, j, col, f, sat);
-            }
-        } else if constexpr (KFIX > 0) {
-            clause_value_fixed<VW, KFIX>(I, t, j, col, f, sat);
-        } else {
-            int beg, end;
-            clause_range(I, kfix, j, beg, end);
-            clause_value<VW, false>(I, t, beg, end, col, f, sat);
-        }
+        return;
     }
+    bool sat[VW];
+    if constexpr (KFIX == 3) {
+        if (I.occx) {
+            const int pos = (o >> 1) & 3;
+            const int own = (own_var << 1) | (o & 1);
+            int L[3];
+            L[0] = pos == 0 ? own : ox.x;
+            L[1] = pos == 0 ? ox.x : (pos == 1 ? own : ox.y);
+            L[2] = pos == 2 ? own : ox.y;
+            float tv[3][VW];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) ldv<VW>(t + (int64_t)(L[p] >> 1) * B + col, tv[p]);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    const float tt = (L[p] & 1) ? -tv[p][e] : tv[p][e];
+                    f[e] = (p == 0) ? tt : f[e] + tt;
+                }
+            }
+        } else {
+            clause_value_fixed<VW, 3>(I, t, j, col, f, sat);
+        }
+    } else if constexpr (KFIX > 0) {
+        clause_value_fixed<VW, KFIX>(I, t, j, col, f, sat);
+    } else {
+        int beg, end;
+        clause_range(I, kfix, j, beg, end);
+        clause_value<VW, false>(I, t, beg, end, col, f, sat);
+    }
+}
+
+// Occurrence term for VW restarts: +-((float)w_j * f_j) * (2/W_U) where
+// clause j is unsat (bit set in nib), +0 elsewhere.
+template <int VW>
+__device__ __forceinline__ void term_from_f(const DevInst &I, int o, uint32_t nib,
+                                            const float (&f)[VW], const float (&cs)[VW],
+                                            float (&term)[VW]) {
+    const int j = o >> I.occ_shift;
+    const bool neg = o & 1;
     const float wj = I.w ? (float)__ldg(I.w + j) : 1.0f;
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
@@ -577,9 +581,13 @@ __global__ void __launch_bounds__(kThreads)
         }
         D.cscale[b] = c > 0 ? 2.0f / (float)c : 0.0f;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         StepScalars *sc = D.sc;
         sc->counter = 0;
+        long long tot = 0;
+        for (int b = 0; b < B; ++b) tot += D.cost[b];
+        sc->dense = (double)tot * 16.0 > (double)sc->wsum * (double)B;
         if (mode == FWD_STEP) {
             const double p1 = sc->p1 * sc->beta1;
             const double p2 = sc->p2 * sc->beta2;
@@ -596,12 +604,40 @@ int auto_fwd_vw(int B) { return B < 8 ? B : 8; }
 int auto_stage_vw(int B) { return B < 16 ? B : 16; }
 int update_vw(int B) { return B < 4 ? B : 4; }
 
+template <int VW>
+static int fwd_resident(const DevInst &I) {
+    int per_sm = 0;
+    cudaError_t e = I.kfix == 3
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<VW, 3>, kThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward<VW, 0>, kThreads, 0);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 2;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    return per_sm * sms;
+}
+
+// One wave of resident blocks (the grid-stride loop covers the rest), or
+// fewer when the clauses do not fill it.
 int fwd_grid_blocks(const DevInst &I) {
     const int VW = I.fwd_vw;
     const int per_thread = VW <= 4 ? 2 : 1;
     const long long items = (long long)I.m * (I.B / VW);
     long long blocks = (items + per_thread * kThreads - 1) / (per_thread * kThreads);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    int resident;
+    switch (VW) {
+        case 8: resident = fwd_resident<8>(I); break;
+        case 4: resident = fwd_resident<4>(I); break;
+        case 2: resident = fwd_resident<2>(I); break;
+        default: resident = fwd_resident<1>(I); break;
+    }
+    if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
@@ -691,18 +727,26 @@ __global__ void __launch_bounds__(kThreads)
     for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
 
     if (mode != BWD_BITS_ONLY) {
-        // phase 1: the chunk's terms into shared memory, four per thread in flight
+        // phase 1: the chunk's terms into shared memory, four per thread in
+        // flight; when unsat clauses are dense, f is fetched together with
+        // the unsat words instead of after them
+        const bool dense = D.sc->dense != 0;
+        const bool expanded = KFIX == 3 && I.occx != nullptr;
         int o[4];
+        int2 ox[4];
         uint32_t wd[4];
+        float f[4][VW];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
             o[u] = r < cn ? __ldcs(I.occ + cb + r) : 0;
+            ox[u] = (expanded && r < cn) ? __ldcs(I.occx + cb + r) : make_int2(0, 0);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
             wd[u] = r < cn ? __ldg(ubits_word(I, S.ubits, o[u], col)) : 0u;
+            if (dense && r < cn) fetch_f<VW, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], i, col, f[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -712,7 +756,10 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) term[e] = 0.0f;
                 const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
-                if (nib) occ_term_unsat<VW, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], nib, col, i, cb + r, term);
+                if (nib) {
+                    if (!dense) fetch_f<VW, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], i, col, f[u]);
+                    term_from_f<VW>(I, o[u], nib, f[u], cs, term);
+                }
 #pragma unroll
                 for (int e = 0; e < VW; ++e) s_term[r * VW + e] = term[e];
             }
@@ -825,21 +872,39 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int e = 0; e < VS; ++e) cs[e] = D.cscale[colS + e];
         const int items = nocc << sshift;
-        // narrow groups take four items per thread in flight; wide groups
-        // already issue VS/4 row loads per literal
-        constexpr int NB = VS <= 4 ? 4 : 1;
+        // NB items per thread in flight; when unsat clauses are dense, f is
+        // fetched together with the unsat words instead of after them
+        constexpr int NB = VS <= 4 ? 4 : 2;
+        const bool dense = D.sc->dense != 0;
+        const bool expanded = KFIX == 3 && I.occx != nullptr;
         for (int base = threadIdx.x; base < items; base += NB * kThreads) {
-            int o[NB];
+            int o[NB], own[NB];
+            int2 ox[NB];
             uint32_t wd[NB];
+            float f[NB][VS];
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 const int it = base + u * kThreads;
-                o[u] = it < items ? __ldcs(I.occ + s0 + (it >> sshift)) : 0;
+                const int r = it >> sshift;
+                o[u] = it < items ? __ldcs(I.occ + s0 + r) : 0;
+                ox[u] = (expanded && it < items) ? __ldcs(I.occx + s0 + r) : make_int2(0, 0);
+                own[u] = 0;
+                if (expanded) {
+                    // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
+                    int lo = 0, hi = nv - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
+                    }
+                    own[u] = v0 + lo;
+                }
             }
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 const int it = base + u * kThreads;
                 wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], colS)) : 0u;
+                if (dense && it < items)
+                    fetch_f<VS, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], own[u], colS, f[u]);
             }
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
@@ -851,17 +916,8 @@ __global__ void __launch_bounds__(kThreads)
                     for (int e = 0; e < VS; ++e) term[e] = 0.0f;
                     const uint32_t nib = occ_nib<VS>(I, o[u], wd[u], colS);
                     if (nib) {
-                        int own = 0;
-                        if (KFIX == 3 && I.occx) {
-                            // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
-                            int lo = 0, hi = nv - 1;
-                            while (lo < hi) {
-                                const int mid = (lo + hi + 1) >> 1;
-                                if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
-                            }
-                            own = v0 + lo;
-                        }
-                        occ_term_unsat<VS, KFIX>(I, kfix, tcur, S.fstore, cs, o[u], nib, colS, own, s0 + r, term);
+                        if (!dense) fetch_f<VS, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], own[u], colS, f[u]);
+                        term_from_f<VS>(I, o[u], nib, f[u], cs, term);
                     }
                     stv<VS>(sterm + (int64_t)r * B + colS, term);
                 }

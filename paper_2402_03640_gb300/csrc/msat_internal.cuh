@@ -62,7 +62,9 @@ struct StepScalars {
     float a_t, r_t;         // lr / (1 - p1), 1 / sqrt(1 - p2) of the step in flight
     double lr, beta1, beta2, eps;
     float b1f, b2f, omb1f, omb2f, epsf;
-    float pad1;
+    int dense;              // last evaluation left > 1/16 of the clause weight unsat:
+                            // the variable pass fetches f before testing the unsat bits
+    long long wsum;         // sum of all clause weights
 };
 
 // Per-restart step state plus scratch.
