@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 int auto_fwd_vw(int B) { return B < 8 ? B : 8; }
-int auto_stage_vw(int B) { return B < 16 ? B : 16; }
+int auto_stage_vw(int B) { return B < 8 ? B : 8; }
 int update_vw(int B) { return B < 4 ? B : 4; }
 
 template <int VW>
