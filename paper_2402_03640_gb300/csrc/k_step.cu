@@ -468,8 +468,18 @@ __global__ void __launch_bounds__(kThreads)
         wacc[e] = 0ull;
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += NU * stride) {
+    const long long base0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    int Lnext[NU][KFIX > 0 ? KFIX : 1];
+    if constexpr (KFIX > 0) {
+#pragma unroll
+        for (int h = 0; h < NU; ++h) {
+            const long long it = base0 + h * stride + lane;
+            const int jn = it < total ? (int)(it / G) : 0;
+#pragma unroll
+            for (int p = 0; p < KFIX; ++p) Lnext[h][p] = base0 < total ? __ldg(I.lit + jn * KFIX + p) : 0;
+        }
+    }
+    for (long long base = base0; base < total; base += NU * stride) {
         long long item[NU];
         bool act[NU];
         int jj[NU];
@@ -482,12 +492,24 @@ __global__ void __launch_bounds__(kThreads)
         float f[NU][VW];
         bool sat[NU][VW];
         if constexpr (KFIX > 0) {
-            // every clause's literals, then every clause's rows
+            // this iteration's literals were loaded one iteration ahead;
+            // load the next iteration's now, then gather this one's rows
             int L[NU][KFIX];
 #pragma unroll
             for (int h = 0; h < NU; ++h)
 #pragma unroll
-                for (int p = 0; p < KFIX; ++p) L[h][p] = __ldg(I.lit + jj[h] * KFIX + p);
+                for (int p = 0; p < KFIX; ++p) L[h][p] = Lnext[h][p];
+            {
+                const long long nb = base + NU * stride;
+#pragma unroll
+                for (int h = 0; h < NU; ++h) {
+                    const long long it = nb + h * stride + lane;
+                    const int jn = it < total ? (int)(it / G) : 0;
+#pragma unroll
+                    for (int p = 0; p < KFIX; ++p)
+                        Lnext[h][p] = nb < total ? __ldg(I.lit + jn * KFIX + p) : 0;
+                }
+            }
             float tv[NU][KFIX][VW];
 #pragma unroll
             for (int h = 0; h < NU; ++h)
@@ -846,6 +868,7 @@ __global__ void __launch_bounds__(kThreads)
     extern __shared__ float4 dyn_smem[];
     __shared__ int s_voff[kThreads + 1];
     const int B = I.B;
+    const bool expanded = KFIX == 3 && I.occx != nullptr;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
     const float *tcur;
     float *tnext;
@@ -862,6 +885,14 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     const int s0 = s_voff[0];
     const int nocc = s_voff[nv] - s0;
+    // expanded records name the other literals only: the block's variable of
+    // each staged row comes from this owner table (rows after the term rows)
+    uint8_t *s_owner = reinterpret_cast<uint8_t *>(sterm + (int64_t)I.occ_cap * B);
+    if (expanded && mode != BWD_BITS_ONLY) {
+        for (int v = threadIdx.x; v < nv; v += kThreads)
+            for (int r = s_voff[v] - s0; r < s_voff[v + 1] - s0; ++r) s_owner[r] = (uint8_t)v;
+        __syncthreads();
+    }
 
     if (mode != BWD_BITS_ONLY) {
         // phase 1: occurrence terms into shared memory, four items per thread in flight
@@ -874,9 +905,8 @@ __global__ void __launch_bounds__(kThreads)
         const int items = nocc << sshift;
         // NB items per thread in flight; when unsat clauses are dense, f is
         // fetched together with the unsat words instead of after them
-        constexpr int NB = VS <= 4 ? 4 : 2;
+        constexpr int NB = VS <= 8 ? 4 : 2;
         const bool dense = D.sc->dense != 0;
-        const bool expanded = KFIX == 3 && I.occx != nullptr;
         for (int base = threadIdx.x; base < items; base += NB * kThreads) {
             int o[NB], own[NB];
             int2 ox[NB];
@@ -888,16 +918,7 @@ __global__ void __launch_bounds__(kThreads)
                 const int r = it >> sshift;
                 o[u] = it < items ? __ldcs(I.occ + s0 + r) : 0;
                 ox[u] = (expanded && it < items) ? __ldcs(I.occx + s0 + r) : make_int2(0, 0);
-                own[u] = 0;
-                if (expanded) {
-                    // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
-                    int lo = 0, hi = nv - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
-                    }
-                    own[u] = v0 + lo;
-                }
+                own[u] = (expanded && it < items) ? v0 + s_owner[r] : 0;
             }
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
@@ -984,7 +1005,8 @@ static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const 
         if (e) return e;
     }
     const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
-    const size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
+    size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
+    if (I.occx) smem += ((size_t)I.occ_cap + 15) & ~(size_t)15;  // owner table
     k_backward_light<VS, VU, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
                                                                                gscale, grad_out);
     return cudaGetLastError();
