@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(kThreads)
         const int items = nocc << sshift;
         // NB items per thread in flight; when unsat clauses are dense, f is
         // fetched together with the unsat words instead of after them
-        constexpr int NB = VS <= 8 ? 4 : 2;
+        constexpr int NB = VS <= 4 ? 4 : 2;
         const bool dense = D.sc->dense != 0;
         for (int base = threadIdx.x; base < items; base += NB * kThreads) {
             int o[NB], own[NB];
