@@ -235,9 +235,7 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
         return fail(MSAT_EINVAL, "msat_create: fwd_blocks >= 0 and light_rows 0 or >= 16");
     // light blocks stage occ_cap occurrence rows of B floats in shared memory;
     // a variable with more occurrences is split into 1024-occurrence chunks
-    // (expanded records add a one-byte owner entry per staged row)
-    const bool may_expand = cfg.f_mode == MSAT_F_EXPANDED || cfg.f_mode == MSAT_F_AUTO;
-    int32_t occ_cap = (kLightSmem - 16) / (int32_t)(sizeof(float) * B + (may_expand ? 1 : 0));
+    int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
     if (cfg.light_rows > 0) occ_cap = std::min(occ_cap, cfg.light_rows);
     if (cfg.f_mode < MSAT_F_AUTO || cfg.f_mode > MSAT_F_EXPANDED)
         return fail(MSAT_EINVAL, "msat_create: unknown f_mode");

@@ -468,18 +468,8 @@ __global__ void __launch_bounds__(kThreads)
         wacc[e] = 0ull;
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
-    const long long base0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-    int Lnext[NU][KFIX > 0 ? KFIX : 1];
-    if constexpr (KFIX > 0) {
-#pragma unroll
-        for (int h = 0; h < NU; ++h) {
-            const long long it = base0 + h * stride + lane;
-            const int jn = it < total ? (int)(it / G) : 0;
-#pragma unroll
-            for (int p = 0; p < KFIX; ++p) Lnext[h][p] = base0 < total ? __ldg(I.lit + jn * KFIX + p) : 0;
-        }
-    }
-    for (long long base = base0; base < total; base += NU * stride) {
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += NU * stride) {
         long long item[NU];
         bool act[NU];
         int jj[NU];
@@ -492,24 +482,12 @@ __global__ void __launch_bounds__(kThreads)
         float f[NU][VW];
         bool sat[NU][VW];
         if constexpr (KFIX > 0) {
-            // this iteration's literals were loaded one iteration ahead;
-            // load the next iteration's now, then gather this one's rows
+            // every clause's literals, then every clause's rows
             int L[NU][KFIX];
 #pragma unroll
             for (int h = 0; h < NU; ++h)
 #pragma unroll
-                for (int p = 0; p < KFIX; ++p) L[h][p] = Lnext[h][p];
-            {
-                const long long nb = base + NU * stride;
-#pragma unroll
-                for (int h = 0; h < NU; ++h) {
-                    const long long it = nb + h * stride + lane;
-                    const int jn = it < total ? (int)(it / G) : 0;
-#pragma unroll
-                    for (int p = 0; p < KFIX; ++p)
-                        Lnext[h][p] = nb < total ? __ldg(I.lit + jn * KFIX + p) : 0;
-                }
-            }
+                for (int p = 0; p < KFIX; ++p) L[h][p] = __ldg(I.lit + jj[h] * KFIX + p);
             float tv[NU][KFIX][VW];
 #pragma unroll
             for (int h = 0; h < NU; ++h)
@@ -868,7 +846,6 @@ __global__ void __launch_bounds__(kThreads)
     extern __shared__ float4 dyn_smem[];
     __shared__ int s_voff[kThreads + 1];
     const int B = I.B;
-    const bool expanded = KFIX == 3 && I.occx != nullptr;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
     const float *tcur;
     float *tnext;
@@ -885,14 +862,6 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     const int s0 = s_voff[0];
     const int nocc = s_voff[nv] - s0;
-    // expanded records name the other literals only: the block's variable of
-    // each staged row comes from this owner table (rows after the term rows)
-    uint8_t *s_owner = reinterpret_cast<uint8_t *>(sterm + (int64_t)I.occ_cap * B);
-    if (expanded && mode != BWD_BITS_ONLY) {
-        for (int v = threadIdx.x; v < nv; v += kThreads)
-            for (int r = s_voff[v] - s0; r < s_voff[v + 1] - s0; ++r) s_owner[r] = (uint8_t)v;
-        __syncthreads();
-    }
 
     if (mode != BWD_BITS_ONLY) {
         // phase 1: occurrence terms into shared memory, four items per thread in flight
@@ -907,6 +876,7 @@ __global__ void __launch_bounds__(kThreads)
         // fetched together with the unsat words instead of after them
         constexpr int NB = VS <= 4 ? 4 : 2;
         const bool dense = D.sc->dense != 0;
+        const bool expanded = KFIX == 3 && I.occx != nullptr;
         for (int base = threadIdx.x; base < items; base += NB * kThreads) {
             int o[NB], own[NB];
             int2 ox[NB];
@@ -918,7 +888,16 @@ __global__ void __launch_bounds__(kThreads)
                 const int r = it >> sshift;
                 o[u] = it < items ? __ldcs(I.occ + s0 + r) : 0;
                 ox[u] = (expanded && it < items) ? __ldcs(I.occx + s0 + r) : make_int2(0, 0);
-                own[u] = (expanded && it < items) ? v0 + s_owner[r] : 0;
+                own[u] = 0;
+                if (expanded) {
+                    // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
+                    int lo = 0, hi = nv - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
+                    }
+                    own[u] = v0 + lo;
+                }
             }
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
@@ -1005,8 +984,7 @@ static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const 
         if (e) return e;
     }
     const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
-    size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
-    if (I.occx) smem += ((size_t)I.occ_cap + 15) & ~(size_t)15;  // owner table
+    const size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
     k_backward_light<VS, VU, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
                                                                                gscale, grad_out);
     return cudaGetLastError();
