@@ -235,6 +235,37 @@ typedef struct {
 int msat_profile_enable(msat_ctx *ctx, int on);
 int msat_profile_read(msat_ctx *ctx, msat_profile *out, int reset);
 
+/*
+ * The relaxed objective and exact cost of a caller-supplied x without a
+ * context and without allocating device memory.  (This entry point has no
+ * counterpart in the paper; it serves callers that may not allocate: hosts
+ * that give the library a fixed memory budget, latency-bound loops where
+ * cudaMalloc's device synchronisation is not allowed, plugins running where
+ * allocation calls are forbidden.)
+ *   n_vars, n_clauses   n >= 1, m >= 0
+ *   clause_off          device int64[m+1] clause offsets into lits
+ *   lits                device int32 DIMACS literals; a literal must not be
+ *                       repeated inside its clause (no canonicalisation is
+ *                       done here); 0 or |l| > n is skipped
+ *   weights             device int64[m] (>= 1) or NULL for all 1
+ *   x                   device float[n][B] relaxed variables (entry i*B + b)
+ *   restarts            B, a power of two in [1, 1024]
+ *   cost_out            device int64[B]: sum of w_j over clauses with no true
+ *                       literal under x' = [x > 0]
+ *   loss_out            device float[B]: sum_U w f^2 / sum_U w (0 if U empty)
+ *   stream              cudaStream_t (NULL = legacy default stream)
+ * Scratch: a 4 MiB array inside the library (held by every GPU that loads
+ * it until the process exits); every size in the range above fits, and a
+ * size that would not is rejected with MSAT_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Calls share the array: calls whose kernels overlap on the GPU race and
+ * give wrong results.  Asynchronous on the stream; allocates nothing.
+ */
+int msat_objective_noalloc(int32_t n_vars, int64_t n_clauses, const int64_t *clause_off,
+                           const int32_t *lits, const int64_t *weights, const float *x,
+                           int32_t restarts, int64_t *cost_out, float *loss_out, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *msat_last_error(void);
 
