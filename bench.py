@@ -349,14 +349,13 @@ def run_ours(args):
 
 
 def kernel_hash():
-    """Hash of the kernel sources, to tell whether stored ncu traffic is stale."""
+    """Hash of the step-kernel sources, to tell whether stored ncu traffic is stale."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_03640_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in ("k_step.cu", "msat_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
