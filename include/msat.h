@@ -153,10 +153,20 @@ int msat_step_ex(msat_ctx *ctx, int32_t n_steps, uint32_t flags, float *loss_out
  *   cost_out    device int64[nb]: sum of w_j over clauses with no true literal
  *   backend     MSAT_BACKEND_SPARSE or MSAT_BACKEND_DENSE
  * Asynchronous on the context stream; the result is exact for both
- * backends.
+ * backends.  The dense backend multiplies the clause matrix W^T (e4m3,
+ * m x n, built on its first use: m_pad * n_pad bytes, rejected above
+ * 64 GiB) by the batch on the tensor cores; it needs weights below 2^25.
  */
 int msat_evaluate(msat_ctx *ctx, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
                   int32_t backend);
+
+/*
+ * Wait for the context's stream and report a device-side failure that the
+ * asynchronous calls could not return: MSAT_ETIMEOUT when a bounded wait in
+ * a kernel (the dense backend's pipeline barriers) gave up; the flag is
+ * cleared.  0 otherwise.
+ */
+int msat_check(msat_ctx *ctx);
 
 /*
  * Best assignment and cost seen so far per restart (Alg. 1 lines 5-7).

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -54,6 +55,13 @@ struct msat_ctx {
     bool probe_ready = false;
     DevState PS{};
     DevStep PD{};
+
+    // dense tensor-core evaluation, set up on first use
+    std::vector<int32_t> clen;    // canonical clause lengths
+    std::vector<uint8_t> taut;    // clause holds some x and not x
+    std::vector<int64_t> wts;     // clause weights (empty: all 1)
+    bool dense_ready = false;
+    DenseDev dense;
 
     // kernel timing (msat_profile_*): event pairs around each launch
     bool prof_on = false;
@@ -109,6 +117,9 @@ static int dalloc_t(msat_ctx *c, T **p, size_t count) {
 static void free_all(msat_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    if (c->dense.Xt) cudaFree(c->dense.Xt);
+    c->dense.Xt = nullptr;
+    c->dense.xt_bytes = 0;
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
     c->prof_kind.clear();
@@ -308,6 +319,19 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     c->max_len = max_len;
     c->max_deg = max_deg;
     c->wsum = wsum;
+    c->clen.resize((size_t)m);
+    c->taut.assign((size_t)m, 0);
+    for (int64_t j = 0; j < m; ++j) {
+        const int32_t b0 = coff[(size_t)j], b1 = coff[(size_t)j + 1];
+        c->clen[(size_t)j] = b1 - b0;
+        for (int32_t p = b0; p < b1 && !c->taut[(size_t)j]; ++p)
+            for (int32_t q = p + 1; q < b1; ++q)
+                if ((lit[(size_t)p] >> 1) == (lit[(size_t)q] >> 1)) {
+                    c->taut[(size_t)j] = 1;
+                    break;
+                }
+    }
+    if (weights) c->wts.assign(weights, weights + m);
 
     const int64_t nB = (int64_t)n_vars * B;
     int rc = MSAT_OK;
@@ -505,6 +529,61 @@ extern "C" int msat_profile_read(msat_ctx *c, msat_profile *out, int reset) {
     return MSAT_OK;
 }
 
+// First use of the dense backend: the e4m3 clause matrix W^T [m_pad][n_pad]
+// (zero padding), per-clause targets -len_j (NaN for padding rows and for
+// clauses holding some x and not x, which are never unsat), 32-bit weights
+// and the TMA descriptor of W^T.
+static int dense_setup(msat_ctx *c) {
+    if (c->dense_ready) return MSAT_OK;
+    for (int64_t w : c->wts)
+        if (w >= (1LL << 25))
+            return fail(MSAT_EINVAL, "msat_evaluate: the dense backend needs clause weights below 2^25");
+    DenseDev &d = c->dense;
+    d.m_pad = (int)std::max<int64_t>(128, (c->m + 127) / 128 * 128);
+    d.n_pad = (c->n + 127) / 128 * 128;
+    const double bytes = (double)d.m_pad * (double)d.n_pad;
+    if (bytes > 64.0 * (1LL << 30))
+        return fail(MSAT_EINVAL, "msat_evaluate: the dense clause matrix would take " +
+                                     std::to_string((long long)(bytes / (1 << 20))) + " MiB (limit 64 GiB)");
+    int rc;
+    if ((rc = dalloc_t(c, &d.Wt, (size_t)d.m_pad * d.n_pad))) return rc;
+    if ((rc = dalloc_t(c, &d.target, (size_t)d.m_pad))) return rc;
+    if ((rc = dalloc_t(c, &d.wgt, (size_t)d.m_pad))) return rc;
+    if ((rc = dalloc_t(c, &d.errflag, 1))) return rc;
+    std::vector<float> tgt((size_t)d.m_pad, std::nanf(""));
+    std::vector<uint32_t> w32((size_t)d.m_pad, 0u);
+    for (int64_t j = 0; j < c->m; ++j) {
+        if (!c->taut[(size_t)j]) tgt[(size_t)j] = -(float)c->clen[(size_t)j];
+        w32[(size_t)j] = c->wts.empty() ? 1u : (uint32_t)c->wts[(size_t)j];
+    }
+    cudaStream_t st = c->stream;
+    MSAT_CUDA_TRY(cudaMemsetAsync(d.Wt, 0, (size_t)d.m_pad * d.n_pad, st));
+    MSAT_CUDA_TRY(cudaMemsetAsync(d.errflag, 0, sizeof(unsigned), st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(d.target, tgt.data(), sizeof(float) * tgt.size(), cudaMemcpyHostToDevice, st));
+    MSAT_CUDA_TRY(cudaMemcpyAsync(d.wgt, w32.data(), sizeof(uint32_t) * w32.size(), cudaMemcpyHostToDevice, st));
+    cudaError_t e = launch_dense_fill(c->I, d.Wt, d.n_pad, st);
+    if (e) return cuda_fail(e, "msat_evaluate: dense matrix fill");
+    MSAT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above are freed on return
+    if ((rc = dense_encode_a(d))) return rc;
+    c->dense_ready = true;
+    return MSAT_OK;
+}
+
+extern "C" int msat_check(msat_ctx *c) {
+    if (!c) return fail(MSAT_EINVAL, "msat_check: ctx is NULL");
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->dense.errflag) {
+        unsigned flag = 0;
+        MSAT_CUDA_TRY(cudaMemcpy(&flag, c->dense.errflag, sizeof(flag), cudaMemcpyDeviceToHost));
+        if (flag) {
+            MSAT_CUDA_TRY(cudaMemset(c->dense.errflag, 0, sizeof(unsigned)));
+            return fail(MSAT_ETIMEOUT, "a bounded wait in the dense evaluation kernel gave up (flag " +
+                                           std::to_string(flag) + ")");
+        }
+    }
+    return MSAT_OK;
+}
+
 extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
                              int32_t backend) {
     if (!c) return fail(MSAT_EINVAL, "msat_evaluate: ctx is NULL");
@@ -517,8 +596,37 @@ extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, 
         if (e) return cuda_fail(e, "msat_evaluate: sparse kernel");
         return MSAT_OK;
     }
-    if (backend == MSAT_BACKEND_DENSE)
-        return fail(MSAT_EINVAL, "msat_evaluate: the dense backend is not available in this build");
+    if (backend == MSAT_BACKEND_DENSE) {
+        int rc = dense_setup(c);
+        if (rc) return rc;
+        const int rows = dense_rows(nb), ntile = dense_tile_n(nb);
+        const size_t need = (size_t)rows * c->dense.n_pad;
+        if (need > c->dense.xt_bytes) {
+            if (c->dense.Xt) {
+                cudaStreamSynchronize(c->stream);
+                cudaFree(c->dense.Xt);
+                c->dense.Xt = nullptr;
+                c->dense.xt_bytes = 0;
+            }
+            cudaError_t e = cudaMalloc(&c->dense.Xt, need);
+            if (e) {
+                cudaGetLastError();
+                c->dense.Xt = nullptr;
+                return fail(MSAT_ENOMEM, "msat_evaluate: dense assignment buffer allocation failed");
+            }
+            c->dense.xt_bytes = need;
+            c->dense.tmB_rows = 0;
+        }
+        if (c->dense.tmB_rows != rows || c->dense.tmB_ntile != ntile) {
+            rc = dense_encode_b(c->dense, rows, ntile);
+            if (rc) return rc;
+        }
+        prof_begin(c, PROF_EVAL);
+        cudaError_t e = launch_dense_eval(c->dense, assign_pm1, c->n, nb, (long long *)cost_out, c->stream);
+        prof_end(c);
+        if (e) return cuda_fail(e, "msat_evaluate: dense kernels");
+        return MSAT_OK;
+    }
     return fail(MSAT_EINVAL, "msat_evaluate: unknown backend");
 }
 

@@ -1,0 +1,390 @@
+// Dense evaluation of a batch of +-1 assignments on the 5th-generation
+// tensor cores (sm_103a): S = W^T X, with W^T the m x n clause matrix
+// (W_ij = +1 for x_i in c_j, -1 for not x_i, 0 otherwise; Sec. 4) and X the
+// n x nb batch of assignments read as +-1.  Clause j is unsatisfied by
+// assignment b iff S_jb = -len_j (the paper's unsat test, Sec. 4
+// "Unsatisfiable Cores", with x' read as +-1), and cost_b = sum_j w_j
+// [S_jb = -len_j].
+//
+// tcgen05.mma .kind::i8 is not available on sm_103a, so both operands are
+// e4m3 (0, +1, -1 are exact) with fp32 accumulation, which is exact here:
+// every partial sum is an integer of magnitude <= n < 2^24.
+//
+// Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 128
+// variables per stage.  Warp 0 (one lane) loads A and B tiles with TMA into
+// a 4-stage ring of 128B-swizzled shared-memory buffers; warp 1 (one lane)
+// issues tcgen05.mma into a TMEM accumulator and releases each stage with
+// tcgen05.commit; warps 2-5 read the accumulator with tcgen05.ld (one TMEM
+// lane quarter each), compare with -len_j and reduce the weighted unsat
+// counts per column.  Every mbarrier wait is bounded: on a timeout the block
+// records an error flag, stops issuing work and still frees its TMEM.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "msat_internal.cuh"
+
+namespace msat {
+
+namespace {
+
+constexpr int kTM = 128;            // clauses per tile (MMA M)
+constexpr int kTK = 128;            // variables per stage (128 bytes of e4m3)
+constexpr int kStages = 4;
+constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
+constexpr long long kSpin = 1LL << 26;
+constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
+
+struct DenseHeader {
+    unsigned long long full[kStages];
+    unsigned long long empty[kStages];
+    unsigned long long done;
+    uint32_t tmem;
+    int abort;
+    unsigned long long colsum[256];
+};
+static_assert(sizeof(DenseHeader) <= kHeader, "dense header does not fit");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier phase; false after kSpin tries.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= 1ull << 46;                   // descriptor version
+    d |= 2ull << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f8f6f4: D fp32, A and B e4m3, both
+// K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_e4m3(int n) {
+    return (1u << 4)                      // D format fp32
+           | (0u << 7) | (0u << 10)       // A, B format e4m3
+           | ((uint32_t)(n >> 3) << 17)   // N / 8
+           | ((uint32_t)(kTM >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kDenseThreads, 1)
+    k_dense_eval(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const float *__restrict__ target, const uint32_t *__restrict__ wgt, int kt_count,
+                 int ntile, int tmem_cols, int nb, unsigned long long *__restrict__ cost,
+                 unsigned int *__restrict__ errflag) {
+    extern __shared__ uint8_t dsm_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
+    DenseHeader *H = reinterpret_cast<DenseHeader *>(base);
+    uint8_t *stages = base + kHeader;
+    const uint32_t a_bytes = kTM * kTK;
+    const uint32_t b_bytes = (uint32_t)ntile * kTK;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTM;
+    const int n0 = blockIdx.y * ntile;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&H->full[s], 1);
+            mbar_init(&H->empty[s], 1);
+        }
+        mbar_init(&H->done, 1);
+        H->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) H->colsum[c] = 0ull;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&H->tmem)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = H->tmem;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of the A (clause rows) and B (assignment rows) tiles
+        int issued = 0;
+        for (int kt = 0; kt < kt_count; ++kt) {
+            const int s = kt % kStages;
+            if (kt >= kStages) {
+                const uint32_t parity = (uint32_t)((kt / kStages - 1) & 1);
+                if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, kSpin)) {
+                    H->abort = 1;
+                    atomicOr(errflag, 1u);
+                    break;
+                }
+            }
+            uint8_t *sa = stages + (size_t)s * stage_bytes;
+            mbar_expect_tx(&H->full[s], stage_bytes);
+            tma_load_2d(sa, &tmA, kt * kTK, m0, &H->full[s]);
+            tma_load_2d(sa + a_bytes, &tmB, kt * kTK, n0, &H->full[s]);
+            issued = kt + 1;
+        }
+        // every issued copy has landed before the block may exit
+        for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
+            if (!mbar_wait(&H->full[kt % kStages], (uint32_t)((kt / kStages) & 1), kSpin)) atomicOr(errflag, 2u);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_e4m3(ntile);
+        for (int kt = 0; kt < kt_count; ++kt) {
+            const int s = kt % kStages;
+            if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((kt / kStages) & 1), kSpin)) {
+                H->abort = 1;
+                atomicOr(errflag, 1u);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stages + (size_t)s * stage_bytes);
+            const uint64_t adesc = smem_desc_sw128(sa);
+            const uint64_t bdesc = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+            for (int kk = 0; kk < kTK / 32; ++kk)  // K = 32 bytes per MMA: +2 in the 16-byte address field
+                mma_e4m3(tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt | kk) != 0);
+            mma_commit(&H->empty[s]);
+        }
+        mma_commit(&H->done);  // arrives once every MMA issued above has completed
+    } else if (warp >= 2) {
+        // epilogue: TMEM lane quarter q holds clause rows m0 + 32q .. + 31
+        const bool ok = mbar_wait(&H->done, 0u, 4 * kSpin);
+        if (!ok) atomicOr(errflag, 4u);
+        tc_fence_after();
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        const float tgt = __ldg(target + row);
+        const uint32_t w = __ldg(wgt + row);
+        if (ok && !*(volatile int *)&H->abort) {
+            for (int c0 = 0; c0 < ntile; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+                uint32_t mine = 0;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const uint32_t hit = (__uint_as_float(v[c]) == tgt) ? w : 0u;
+                    const uint32_t sum = __reduce_add_sync(0xffffffffu, hit);
+                    if (lane == c) mine = sum;
+                }
+                if (mine) atomicAdd(&H->colsum[c0 + lane], (unsigned long long)mine);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (!H->abort)
+        for (int c = threadIdx.x; c < ntile; c += blockDim.x) {
+            const int col = n0 + c;
+            if (col < nb && H->colsum[c]) atomicAdd(cost + col, H->colsum[c]);
+        }
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// W^T in e4m3: row j holds +1 / -1 at the columns of the clause's literals
+// (the buffer was zeroed).  A clause with x and not x writes both; its target
+// is NaN, so it never counts.
+__global__ void k_dense_fill(DevInst I, uint8_t *__restrict__ Wt, int n_pad) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < I.m;
+         j += (long long)gridDim.x * blockDim.x) {
+        int beg, end;
+        if (I.kfix > 0) {
+            beg = (int)j * I.kfix;
+            end = beg + I.kfix;
+        } else {
+            beg = I.coff[j];
+            end = I.coff[j + 1];
+        }
+        for (int p = beg; p < end; ++p) {
+            const int L = I.lit[p];
+            Wt[j * n_pad + (L >> 1)] = (L & 1) ? kE4M3MinusOne : kE4M3One;
+        }
+    }
+}
+
+// X^T in e4m3 from the caller's int8 [n][nb] batch (> 0 is true): rows =
+// assignments, n_pad columns, zero padding; 32 x 32 tiles through shared
+// memory so both sides are coalesced.
+__global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uint8_t *__restrict__ Xt,
+                                int n_pad, int rows) {
+    __shared__ uint8_t tile[32][33];
+    const int v0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int v = v0 + r, b = b0 + threadIdx.x;
+        uint8_t e = 0;
+        if (v < n && b < nb) e = a[(long long)v * nb + b] > 0 ? kE4M3One : kE4M3MinusOne;
+        tile[r][threadIdx.x] = e;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r, v = v0 + threadIdx.x;
+        if (b < rows && v < n_pad) Xt[(long long)b * n_pad + v] = tile[threadIdx.x][r];
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2D uint8 tensor [rows][cols] (cols contiguous), box 128 x box_rows, 128B swizzle.
+int encode_2d(CUtensorMap *map, void *base, long long cols, long long rows, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return fail(MSAT_ECUDA, "dense backend: cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols};
+    const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(MSAT_ECUDA, "dense backend: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return MSAT_OK;
+}
+
+}  // namespace
+
+int dense_tile_n(int nb) {
+    const int nb16 = (nb + 15) / 16 * 16;
+    return nb16 <= 256 ? nb16 : 256;
+}
+
+int dense_rows(int nb) {
+    const int nt = dense_tile_n(nb);
+    return (nb + nt - 1) / nt * nt;
+}
+
+size_t dense_smem_bytes(int ntile) {
+    return 1024 + kHeader + (size_t)kStages * ((size_t)kTM * kTK + (size_t)ntile * kTK);
+}
+
+int dense_encode_a(DenseDev &d) { return encode_2d(&d.tmA, d.Wt, d.n_pad, d.m_pad, kTM); }
+
+int dense_encode_b(DenseDev &d, int rows, int ntile) {
+    d.tmB_rows = rows;
+    d.tmB_ntile = ntile;
+    return encode_2d(&d.tmB, d.Xt, d.n_pad, rows, ntile);
+}
+
+cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStream_t st) {
+    long long blocks = ((long long)I.m + kThreads - 1) / kThreads;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_dense_fill<<<(unsigned)blocks, kThreads, 0, st>>>(I, Wt, n_pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_eval(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
+                              cudaStream_t st) {
+    const int ntile = d.tmB_ntile;
+    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
+    k_dense_convert<<<cg, cb, 0, st>>>(a, n, nb, d.Xt, d.n_pad, d.tmB_rows);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    e = cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);
+    if (e) return e;
+    const size_t smem = dense_smem_bytes(ntile);
+    e = cudaFuncSetAttribute(k_dense_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_dense());
+    if (e) return e;
+    int tmem_cols = 32;
+    while (tmem_cols < ntile) tmem_cols <<= 1;
+    dim3 grid((unsigned)(d.m_pad / kTM), (unsigned)(d.tmB_rows / ntile));
+    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, d.n_pad / kTK, ntile,
+                                                   tmem_cols, nb, reinterpret_cast<unsigned long long *>(cost),
+                                                   d.errflag);
+    return cudaGetLastError();
+}
+
+size_t smem_max_dense() { return dense_smem_bytes(256); }
+
+}  // namespace msat

@@ -3,6 +3,7 @@
 // kernels, and the launchers each kernel file provides.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -88,6 +89,21 @@ struct DevState {
     uint32_t *ubits;       // unsat bits, flat index j*B + b
     uint8_t *bestx;        // [n][B] best assignment (0/1)
     float *fstore;         // [m][B] f of the last clause pass, or nullptr: recompute f
+};
+
+// Dense tensor-core evaluation (k_dense.cu): e4m3 clause matrix W^T
+// [m_pad][n_pad], per-row target -len_j (NaN: never unsat), 32-bit weights,
+// the e4m3 assignment batch X^T [rows][n_pad] and their TMA descriptors.
+struct DenseDev {
+    uint8_t *Wt = nullptr;
+    float *target = nullptr;
+    uint32_t *wgt = nullptr;
+    int m_pad = 0, n_pad = 0;
+    uint8_t *Xt = nullptr;
+    size_t xt_bytes = 0;
+    int tmB_rows = 0, tmB_ntile = 0;
+    unsigned int *errflag = nullptr;
+    CUtensorMap tmA, tmB;
 };
 
 // Kernel modes of the variable pass.
@@ -202,5 +218,14 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
                                cudaStream_t st);
+int dense_tile_n(int nb);
+int dense_rows(int nb);
+size_t dense_smem_bytes(int ntile);
+size_t smem_max_dense();
+int dense_encode_a(DenseDev &d);
+int dense_encode_b(DenseDev &d, int rows, int ntile);
+cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStream_t st);
+cudaError_t launch_dense_eval(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
+                              cudaStream_t st);
 
 }  // namespace msat

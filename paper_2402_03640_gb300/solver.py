@@ -174,6 +174,10 @@ class Solver:
         check(self._lib.msat_evaluate(self._ctx, _p(a), nb, _p(out), be))
         return out
 
+    def check(self) -> None:
+        """Raise if a bounded device wait gave up since the last check."""
+        check(self._lib.msat_check(self._ctx))
+
     # ---------------------------------------------------- differentiable
     def forward(self, x):
         import torch

@@ -1,0 +1,69 @@
+"""Dense tensor-core evaluation (e4m3 W^T times the +-1 batch, exact fp32
+accumulation) against the sparse evaluator and the oracle's exact cost:
+bit-exact integers for every assignment."""
+import numpy as np
+import pytest
+
+from synth import Cnf, pigeonhole, uniform_ksat, zipf_weighted
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2402_03640_gb300 as p
+    from paper_2402_03640_gb300 import build
+    build.build()
+    p.load()
+    return p
+
+
+def _batch(n, nb, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 2, size=(nb, n)).astype(np.uint8)
+
+
+def _check(pkg, oracle, cnf, nbs, seed=0):
+    import torch
+    with pkg.Solver.from_cnf(cnf, restarts=1) as s:
+        for nb in nbs:
+            a01 = _batch(cnf.n, nb, seed + nb)
+            want = oracle.cost(cnf, a01)
+            pm1 = torch.from_numpy((2 * a01.astype(np.int8) - 1).T.copy()).cuda()
+            dense = s.evaluate(pm1, backend="dense").cpu().numpy()
+            s.check()
+            sparse = s.evaluate(pm1, backend="sparse").cpu().numpy()
+            assert np.array_equal(sparse, want), f"sparse nb={nb}"
+            assert np.array_equal(dense, want), f"dense nb={nb}"
+
+
+def test_dense_small_batches(pkg, oracle):
+    cnf = uniform_ksat(300, 1290, 3, seed=1)
+    _check(pkg, oracle, cnf, [1, 7, 16, 33, 100, 256])
+
+
+def test_dense_multi_tile_batches(pkg, oracle):
+    cnf = uniform_ksat(700, 3010, 3, seed=2)
+    _check(pkg, oracle, cnf, [257, 300, 513])
+
+
+def test_dense_weighted_mixed_lengths(pkg, oracle):
+    cnf = zipf_weighted(1000, 4000, seed=3)
+    _check(pkg, oracle, cnf, [5, 64, 200])
+
+
+def test_dense_degenerate_and_long_clauses(pkg, oracle):
+    cnf = Cnf.from_clauses(140, [[1, -1, 2], [], [3, 3, -4], [5]] +
+                           [list(range(6, 140))] + [[-7, -8]] * 3, weights=[4, 9, 2, 1, 3, 5, 6, 7])
+    _check(pkg, oracle, cnf, [1, 40])
+    _check(pkg, oracle, pigeonhole(30), [24, 130])
+
+
+def test_dense_config1_full_size(pkg, oracle):
+    """Uniform 3-SAT n=5000, m=21500: the 256-assignment batch of the
+    batched-restarts configuration."""
+    cnf = uniform_ksat(5000, 21500, 3, seed=0)
+    _check(pkg, oracle, cnf, [256])
