@@ -37,7 +37,8 @@ L2_BYTES = 129 * 2 ** 20
 WORKLOADS = {
     # name: (generator, restarts, description)
     "ksat3_n5000_m21500_b256": (lambda: uniform_ksat(5000, 21500, 3, seed=0), 256,
-                                "uniform random 3-SAT, n=5000, m=21500 (seed 0), B=256 restarts, x from seed 1"),
+                                "uniform random 3-SAT, n=5000, m=21500 (seed 0), B=256 restarts, x from seed 1; "
+                                "each step also evaluates the rounded +-1 batch on the tensor cores"),
     "ksat3_n1000000_m4300000_b16": (lambda: uniform_ksat(1000000, 4300000, 3, seed=0), 16,
                                     "uniform random 3-SAT, n=1e6, m=4.3e6 (seed 0), B=16 restarts"),
     "zipf_n200000_m1000000_weighted_b1": (lambda: zipf_weighted(200000, 1000000, seed=0), 1,
@@ -46,6 +47,8 @@ WORKLOADS = {
                           "uniform random 3-SAT, n=50, m=215 (seed 0), B=1"),
 }
 DEFAULT_WORKLOAD = "ksat3_n5000_m21500_b256"
+# workloads whose step also runs the dense tensor-core evaluation of the rounded batch
+DENSE_EVAL = {"ksat3_n5000_m21500_b256"}
 LR = 1e-4
 
 
@@ -64,12 +67,15 @@ def algorithmic_bytes(cnf, B):
 
 
 def measured_peaks():
+    """(HBM GB/s, source), (fp8 dense TFLOP/s, source): the copy bandwidth and
+    the bf16 GEMM rate measured on this machine, fp8 taken as twice bf16 (the
+    nominal ratio of the dense tensor rates)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return (float(d["hbm_gbs"]), "measured"), (2.0 * float(d["bf16_tflops"]), "measured bf16 x 2")
+    return (6800.0, "fallback"), (3800.0, "fallback bf16 x 2")
 
 
 class ClockSampler:
@@ -215,9 +221,13 @@ def run_ours(args):
 
     solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
     stream = torch.cuda.current_stream()
+    dense = args.workload in DENSE_EVAL
+    dense_cost = torch.empty(B, dtype=torch.int64, device="cuda")
 
     def one_step():
         solver.step_async(1, final_eval=False)
+        if dense:
+            solver.evaluate_x("dense", out=dense_cost)
 
     # warm-up, then a short clock-settling run, both untimed
     for _ in range(args.warmup):
@@ -266,16 +276,24 @@ def run_ours(args):
     value = units / (t_max / 1e3)
 
     # roofline of the dominant kernel, from the events around each launch
-    peak, peak_kind = measured_peaks()
+    (peak, peak_kind), (tc_peak, tc_kind) = measured_peaks()
     per_kernel = {}
     for kind in ("forward", "backward"):
         launches, ms = prof[kind]
         if launches:
             avg = ms / launches
-            per_kernel[kind] = {"launches": launches, "avg_us": 1e3 * avg,
-                                "bytes": abytes[kind], "gbs": abytes[kind] / (avg / 1e3) / 1e9}
-    dom = max(per_kernel, key=lambda k: prof[k][1])
-    ach = per_kernel[dom]["gbs"]
+            per_kernel[kind] = {"launches": launches, "avg_us": 1e3 * avg, "bound": "hbm",
+                                "bytes": abytes[kind], "gbs": abytes[kind] / (avg / 1e3) / 1e9,
+                                "frac": abytes[kind] / (avg / 1e3) / 1e9 / peak}
+    if dense and prof["evaluate"][0]:
+        launches, ms = prof["evaluate"]
+        avg = ms / launches
+        flops = 2.0 * cnf.m * cnf.n * B  # multiply-adds of W^T X counted twice
+        tf = flops / (avg / 1e3) / 1e12
+        per_kernel["dense_eval"] = {"launches": launches, "avg_us": 1e3 * avg, "bound": "tensor",
+                                    "flops": flops, "tflops": tf, "frac": tf / tc_peak,
+                                    "peak_tflops": tc_peak, "peak_source": tc_kind}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["avg_us"] * per_kernel[k]["launches"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -284,10 +302,17 @@ def run_ours(args):
         ent = tr.get(args.workload, {}).get(dom)
         if ent and ent.get("kernel_hash") == kernel_hash():
             traffic = ent["bytes_per_launch"]
-    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": traffic, "kernel": dom,
-                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
-                "algorithmic_bytes_per_launch": abytes[dom]}
+    if per_kernel[dom]["bound"] == "tensor":
+        ach = per_kernel[dom]["tflops"]
+        roofline = {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": ach / tc_peak, "traffic": traffic, "kernel": dom,
+                    "peak_source": tc_kind, "algorithmic_flops_per_launch": per_kernel[dom]["flops"]}
+    else:
+        ach = per_kernel[dom]["gbs"]
+        roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": traffic, "kernel": dom,
+                    "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                    "algorithmic_bytes_per_launch": abytes[dom]}
 
     # end to end through the public API with host buffers: upload the CNF
     # from host memory, then per step the call a user makes (step plus the
@@ -317,6 +342,10 @@ def run_ours(args):
     launches = prof["forward"][0] + prof["backward"][0] + prof["evaluate"][0] + prof["other"][0]
     info = solver.info()
     _, cost = solver.step(0, want_loss=False)
+    dense_ok = None
+    if dense:
+        dense_ok = bool(np.array_equal(solver.evaluate_x("dense").cpu().numpy(), cost))
+        solver.check()
     line = {
         "metric": "fwd+bwd literal-evals/s", "value": value, "unit": "literal-evals/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -339,6 +368,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "wall_s_timed": wall1 - wall0,
         "final_cost_min": int(cost.min()),
+        "dense_eval_matches_sparse": dense_ok,
     }
     solver.close()
     if rank == 0:

@@ -161,6 +161,14 @@ int msat_evaluate(msat_ctx *ctx, const int8_t *assign_pm1, int32_t nb, int64_t *
                   int32_t backend);
 
 /*
+ * Exact cost of the context's current x, rounded (x' = [x > 0], Sec. 4) to a
+ * +-1 batch of B assignments by a kernel, with either backend.
+ *   cost_out   device int64[B]
+ * Asynchronous on the context stream.
+ */
+int msat_evaluate_x(msat_ctx *ctx, int32_t backend, int64_t *cost_out);
+
+/*
  * Wait for the context's stream and report a device-side failure that the
  * asynchronous calls could not return: MSAT_ETIMEOUT when a bounded wait in
  * a kernel (the dense backend's pipeline barriers) gave up; the flag is

@@ -62,6 +62,7 @@ struct msat_ctx {
     std::vector<int64_t> wts;     // clause weights (empty: all 1)
     bool dense_ready = false;
     DenseDev dense;
+    int8_t *xpm1 = nullptr;       // rounded x as a +-1 batch, allocated on first use
 
     // kernel timing (msat_profile_*): event pairs around each launch
     bool prof_on = false;
@@ -621,13 +622,31 @@ extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, 
             rc = dense_encode_b(c->dense, rows, ntile);
             if (rc) return rc;
         }
-        prof_begin(c, PROF_EVAL);
-        cudaError_t e = launch_dense_eval(c->dense, assign_pm1, c->n, nb, (long long *)cost_out, c->stream);
+        prof_begin(c, PROF_OTHER);
+        cudaError_t e = launch_dense_convert(c->dense, assign_pm1, c->n, nb, (long long *)cost_out, c->stream);
         prof_end(c);
-        if (e) return cuda_fail(e, "msat_evaluate: dense kernels");
+        if (e) return cuda_fail(e, "msat_evaluate: dense batch conversion");
+        prof_begin(c, PROF_EVAL);
+        e = launch_dense_gemm(c->dense, nb, (long long *)cost_out, c->stream);
+        prof_end(c);
+        if (e) return cuda_fail(e, "msat_evaluate: dense tensor-core kernel");
         return MSAT_OK;
     }
     return fail(MSAT_EINVAL, "msat_evaluate: unknown backend");
+}
+
+extern "C" int msat_evaluate_x(msat_ctx *c, int32_t backend, int64_t *cost_out) {
+    if (!c || !cost_out) return fail(MSAT_EINVAL, "msat_evaluate_x: NULL argument");
+    const long long nB = (long long)c->n * c->B;
+    if (!c->xpm1) {
+        int rc = dalloc_t(c, &c->xpm1, (size_t)nB);
+        if (rc) return rc;
+    }
+    prof_begin(c, PROF_OTHER);
+    cudaError_t e = launch_round_pm1(c->S.x, c->xpm1, nB, c->stream);
+    prof_end(c);
+    if (e) return cuda_fail(e, "msat_evaluate_x: rounding kernel");
+    return msat_evaluate(c, c->xpm1, c->B, cost_out, backend);
 }
 
 extern "C" int msat_best(msat_ctx *c, uint8_t *assign01, int64_t *best_cost) {

@@ -364,15 +364,18 @@ cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_eval(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
-                              cudaStream_t st) {
-    const int ntile = d.tmB_ntile;
+cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
+                                 cudaStream_t st) {
     dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
     k_dense_convert<<<cg, cb, 0, st>>>(a, n, nb, d.Xt, d.n_pad, d.tmB_rows);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    e = cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);
-    if (e) return e;
+    return cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);
+}
+
+cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st) {
+    const int ntile = d.tmB_ntile;
+    cudaError_t e;
     const size_t smem = dense_smem_bytes(ntile);
     e = cudaFuncSetAttribute(k_dense_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_dense());
     if (e) return e;

@@ -72,4 +72,20 @@ cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long l
     return cudaGetLastError();
 }
 
+// Rounded batch of the relaxed variables: a[q] = +1 if x[q] > 0 else -1
+// (the de-relaxation of Sec. 4, read as +-1), same [n][B] layout.
+__global__ void k_round_pm1(const float *__restrict__ x, int8_t *__restrict__ a, long long count) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x)
+        a[q] = __ldg(x + q) > 0.0f ? (int8_t)1 : (int8_t)-1;
+}
+
+cudaError_t launch_round_pm1(const float *x, int8_t *a, long long count, cudaStream_t st) {
+    long long blocks = (count + kThreads - 1) / kThreads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_round_pm1<<<(unsigned)blocks, kThreads, 0, st>>>(x, a, count);
+    return cudaGetLastError();
+}
+
 }  // namespace msat

@@ -218,6 +218,7 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
                                cudaStream_t st);
+cudaError_t launch_round_pm1(const float *x, int8_t *a, long long count, cudaStream_t st);
 int dense_tile_n(int nb);
 int dense_rows(int nb);
 size_t dense_smem_bytes(int ntile);
@@ -225,7 +226,8 @@ size_t smem_max_dense();
 int dense_encode_a(DenseDev &d);
 int dense_encode_b(DenseDev &d, int rows, int ntile);
 cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStream_t st);
-cudaError_t launch_dense_eval(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
-                              cudaStream_t st);
+cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
+                                 cudaStream_t st);
+cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st);
 
 }  // namespace msat

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),
             "msat_objective_noalloc": ([i32, i64, P, P, P, P, i32, P, P, P], ctypes.c_int),
             "msat_check": ([P], ctypes.c_int),
+            "msat_evaluate_x": ([P, i32, P], ctypes.c_int),
             "msat_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():

@@ -174,6 +174,16 @@ class Solver:
         check(self._lib.msat_evaluate(self._ctx, _p(a), nb, _p(out), be))
         return out
 
+    def evaluate_x(self, backend: str = "sparse", out=None):
+        """Exact cost of the current x rounded to +-1, as a torch int64 CUDA
+        tensor [B] (written into out when given)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.B, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+        be = {"sparse": native.BACKEND_SPARSE, "dense": native.BACKEND_DENSE}[backend]
+        check(self._lib.msat_evaluate_x(self._ctx, be, _p(out)))
+        return out
+
     def check(self) -> None:
         """Raise if a bounded device wait gave up since the last check."""
         check(self._lib.msat_check(self._ctx))

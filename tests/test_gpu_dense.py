@@ -67,3 +67,18 @@ def test_dense_config1_full_size(pkg, oracle):
     batched-restarts configuration."""
     cnf = uniform_ksat(5000, 21500, 3, seed=0)
     _check(pkg, oracle, cnf, [256])
+
+
+def test_evaluate_current_x_both_backends(pkg, oracle):
+    """The rounded batch of the solver's own x: dense, sparse and the cost the
+    step kernels report agree with the oracle after a few steps."""
+    cnf = uniform_ksat(2000, 8600, 3, seed=6)
+    B, S = 64, 5
+    ref = oracle.solve(cnf, B, 1, S, mode=oracle.MODE_F32, lr=3e-2)
+    with pkg.Solver.from_cnf(cnf, restarts=B, lr=3e-2) as s:
+        _, cost = s.step(S, want_loss=False)
+        d = s.evaluate_x("dense").cpu().numpy()
+        sp = s.evaluate_x("sparse").cpu().numpy()
+        s.check()
+    assert np.array_equal(cost, ref["cost_hist"][-1])
+    assert np.array_equal(d, cost) and np.array_equal(sp, cost)
