@@ -284,6 +284,84 @@ int msat_objective_noalloc(int32_t n_vars, int64_t n_clauses, const int64_t *cla
                            const int32_t *lits, const int64_t *weights, const float *x,
                            int32_t restarts, int64_t *cost_out, float *loss_out, void *stream);
 
+/*
+ * Serving: a request loop that runs many instances at once (continuous
+ * batching).  Requests arrive with msat_submit at any time; a scheduler
+ * thread admits them, oldest first, while their device memory fits the
+ * budget and a slot is free, keeps every admitted instance's clause arrays
+ * and optimizer state resident, and advances all of them together: each
+ * iteration of Algorithm 1 for the whole slot table is one captured CUDA
+ * graph (three batched kernels), replayed chunk by chunk.  An instance that
+ * has taken its steps gets one final evaluation; its result is copied out
+ * and its memory returned, and queued requests take the freed room.  Each
+ * instance's arithmetic is independent of the others, so a result is bit
+ * for bit the one msat_create/msat_step(steps)/msat_best gives alone.
+ * (Serving is not part of the paper; the per-instance work is Alg. 1.)
+ */
+typedef struct msat_server msat_server;
+
+typedef struct {
+    size_t hbm_budget;  /* device bytes the resident instances may hold
+                           (0 = half of the free memory at creation)      */
+    int32_t max_slots;  /* instances stepped together (0 = 256)           */
+    int32_t restarts;   /* B of every instance (power of two, <= 1024)    */
+    int32_t chunk;      /* steps per scheduling round (0 = 50)            */
+    int32_t reserved;
+    double lr, beta1, beta2, eps; /* Adam settings of every instance      */
+} msat_server_config;
+
+typedef struct {
+    int32_t n_vars;           /* n >= 1                                   */
+    int32_t steps;            /* optimizer steps to run (>= 0)            */
+    int64_t n_clauses;        /* m >= 0                                   */
+    const int64_t *clause_off; /* host int64[m+1]  (copied at submit)     */
+    const int32_t *lits;      /* host DIMACS int32 (copied at submit)     */
+    const int64_t *weights;   /* host int64[m] or NULL (copied at submit) */
+    uint64_t seed_x;          /* seed of the random start                 */
+} msat_request;
+
+typedef struct {
+    int32_t status;       /* 0 done; MSAT_EAGAIN queued or running; < 0 the
+                             request failed with that code               */
+    int32_t best_restart; /* restart holding best_cost                   */
+    int64_t best_cost;    /* lowest cost over restarts and steps         */
+    int64_t steps;        /* optimizer steps taken                       */
+    int32_t n_vars;
+    int32_t restarts;
+    double queue_ms;      /* submit -> admitted                          */
+    double latency_ms;    /* submit -> result ready                      */
+} msat_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled;
+    int32_t queued, running, peak_running, reserved;
+    int64_t hbm_in_use, hbm_budget, rounds, graph_captures;
+} msat_server_stats;
+
+int msat_server_config_default(msat_server_config *cfg);
+int msat_server_create(msat_server **out, const msat_server_config *cfg);
+/* Stop accepting requests, finish everything admitted or queued, free all. */
+void msat_server_destroy(msat_server *srv);
+
+/* Queue a request (its arrays are copied).  A request that cannot fit the
+ * budget even alone, or a malformed one, fails here (MSAT_EBUDGET /
+ * MSAT_EINVAL) without a ticket. */
+int msat_submit(msat_server *srv, const msat_request *req, uint64_t *ticket);
+
+/* Non-blocking result query.  Returns 0 and fills out (and, when non-NULL,
+ * best_costs int64[B] per restart and assign01 uint8[n] of the best
+ * restart) once the request is done, after which the ticket is forgotten;
+ * MSAT_EAGAIN while it is queued or running; the request's error code if it
+ * failed; MSAT_EINVAL for an unknown ticket. */
+int msat_poll(msat_server *srv, uint64_t ticket, msat_result *out, int64_t *best_costs,
+              uint8_t *assign01);
+/* msat_poll that waits up to timeout_s seconds (MSAT_ETIMEOUT after). */
+int msat_wait(msat_server *srv, uint64_t ticket, double timeout_s, msat_result *out,
+              int64_t *best_costs, uint8_t *assign01);
+/* Withdraw a request that is still queued (MSAT_ESTATE once admitted). */
+int msat_cancel(msat_server *srv, uint64_t ticket);
+int msat_server_get_stats(msat_server *srv, msat_server_stats *out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *msat_last_error(void);
 

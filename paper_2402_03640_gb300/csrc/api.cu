@@ -33,43 +33,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 using namespace msat;
 
-// Device memory of one context.  Every buffer is a separate allocation so
-// each starts on a 256-byte boundary (vector loads need 16 bytes).
-struct msat_ctx {
-    msat_config cfg;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int32_t n = 0, B = 0;
-    int64_t m = 0, nnz = 0;
-    int32_t kfix = 0, max_len = 0, max_deg = 0;
-    int64_t wsum = 0;
-    int64_t steps_done_host = 0;
-    std::vector<void *> allocs;
-    int64_t device_bytes = 0;
-
-    DevInst I{};
-    DevState S{};
-    DevStep D{};
-
-    // probe (autograd) path, allocated on first use
-    bool probe_ready = false;
-    DevState PS{};
-    DevStep PD{};
-
-    // dense tensor-core evaluation, set up on first use
-    std::vector<int32_t> clen;    // canonical clause lengths
-    std::vector<uint8_t> taut;    // clause holds some x and not x
-    std::vector<int64_t> wts;     // clause weights (empty: all 1)
-    bool dense_ready = false;
-    DenseDev dense;
-    int8_t *xpm1 = nullptr;       // rounded x as a +-1 batch, allocated on first use
-
-    // kernel timing (msat_profile_*): event pairs around each launch
-    bool prof_on = false;
-    std::vector<cudaEvent_t> prof_ev;
-    std::vector<int> prof_kind;
-    size_t prof_used = 0;
-};
+#include "ctx.cuh"
 
 enum { PROF_FWD = 0, PROF_BWD = 1, PROF_EVAL = 2, PROF_OTHER = 3 };
 
@@ -98,7 +62,7 @@ static void prof_end(msat_ctx *c) {
 
 static int dalloc(msat_ctx *c, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = c->pool_alloc ? cudaMallocAsync(p, bytes, c->stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -116,7 +80,9 @@ static int dalloc_t(msat_ctx *c, T **p, size_t count) {
 }
 
 static void free_all(msat_ctx *c) {
-    for (void *p : c->allocs) cudaFree(p);
+    for (void *p : c->allocs) {
+        if (c->pool_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
+    }
     c->allocs.clear();
     if (c->dense.Xt) cudaFree(c->dense.Xt);
     c->dense.Xt = nullptr;
@@ -148,6 +114,13 @@ static bool valid_restarts(int32_t B) {
 extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
                            const int64_t *clause_off, const int32_t *lits, const int64_t *weights,
                            const msat_config *cfg_in, void *stream) {
+    return msat::ctx_create(out, n_vars, n_clauses, clause_off, lits, weights, cfg_in,
+                            (cudaStream_t)stream, false);
+}
+
+int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const int64_t *clause_off,
+                     const int32_t *lits, const int64_t *weights, const msat_config *cfg_in,
+                     cudaStream_t stream, bool pool_alloc) {
     if (!out) return fail(MSAT_EINVAL, "msat_create: out is NULL");
     *out = nullptr;
     msat_config cfg;
@@ -310,7 +283,8 @@ extern "C" int msat_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses,
     msat_ctx *c = new (std::nothrow) msat_ctx();
     if (!c) return fail(MSAT_ENOMEM, "msat_create: host allocation failed");
     c->cfg = cfg;
-    c->stream = (cudaStream_t)stream;
+    c->stream = stream;
+    c->pool_alloc = pool_alloc;
     cudaGetDevice(&c->device);
     c->n = n_vars;
     c->B = cfg.restarts;
@@ -459,6 +433,12 @@ extern "C" void msat_destroy(msat_ctx *c) {
     delete c;
 }
 
+void msat::ctx_destroy_async(msat_ctx *c) {
+    if (!c) return;
+    free_all(c);  // pool allocations are released in order on the context stream
+    delete c;
+}
+
 extern "C" int msat_set_stream(msat_ctx *c, void *stream) {
     if (!c) return fail(MSAT_EINVAL, "msat_set_stream: ctx is NULL");
     c->stream = (cudaStream_t)stream;
@@ -466,6 +446,9 @@ extern "C" int msat_set_stream(msat_ctx *c, void *stream) {
 }
 
 // One evaluation of the current x (final evaluation of a msat_step call).
+static cudaError_t eval_current(msat_ctx *c);
+cudaError_t msat::ctx_eval_current(msat_ctx *c) { return eval_current(c); }
+
 static cudaError_t eval_current(msat_ctx *c) {
     prof_begin(c, PROF_FWD);
     cudaError_t e = launch_forward(c->I, c->S, c->D, FWD_EVAL, nullptr, c->stream);

@@ -126,6 +126,47 @@ __device__ __forceinline__ void clause_range(const DevInst &I, int kfix, int j, 
     }
 }
 
+// f_j and sat of a clause longer than 32 literals: 32-literal leaves in
+// order, combined by the dyadic counter.  Kept out of line so its counter
+// registers do not weigh on the common short-clause path.
+template <int VW, bool WANT_SAT>
+__device__ __noinline__ void clause_value_long(const DevInst &I, const float *__restrict__ t,
+                                               int beg, int end, int col, float (&f)[VW],
+                                               bool (&sat)[VW]) {
+    const int B = I.B;
+    LeafCounter<6> lc[VW];
+    float leaf[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+        lc[e].init();
+        sat[e] = false;
+    }
+    int in_leaf = 0;
+    for (int p = beg; p < end; ++p) {
+        const int L = __ldg(I.lit + p);
+        const bool neg = L & 1;
+        float tv[VW];
+        ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const float term = neg ? -tv[e] : tv[e];
+            leaf[e] = (in_leaf == 0) ? term : leaf[e] + term;
+            if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
+        }
+        if (++in_leaf == 32) {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+            in_leaf = 0;
+        }
+    }
+    if (in_leaf) {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) f[e] = lc[e].finish();
+}
+
 // f_j for VW restarts in the fixed order (literal order, 32-literal leaves,
 // dyadic combination) and, if WANT_SAT, whether some literal is true.
 template <int VW, bool WANT_SAT>
@@ -133,53 +174,26 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
                                              int beg, int end, int col, float (&f)[VW],
                                              bool (&sat)[VW]) {
     const int B = I.B;
+    if (end - beg > 32) {
+        clause_value_long<VW, WANT_SAT>(I, t, beg, end, col, f, sat);
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
         f[e] = 0.0f;
         sat[e] = false;
     }
-    if (end - beg <= 32) {
-        for (int p = beg; p < end; ++p) {
-            const int L = __ldg(I.lit + p);
-            const bool neg = L & 1;
-            float tv[VW];
-            ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
+    for (int p = beg; p < end; ++p) {
+        const int L = __ldg(I.lit + p);
+        const bool neg = L & 1;
+        float tv[VW];
+        ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
 #pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const float term = neg ? -tv[e] : tv[e];
-                f[e] = (p == beg) ? term : f[e] + term;
-                if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
-            }
+        for (int e = 0; e < VW; ++e) {
+            const float term = neg ? -tv[e] : tv[e];
+            f[e] = (p == beg) ? term : f[e] + term;
+            if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
         }
-    } else {
-        LeafCounter<6> lc[VW];
-        float leaf[VW];
-#pragma unroll
-        for (int e = 0; e < VW; ++e) lc[e].init();
-        int in_leaf = 0;
-        for (int p = beg; p < end; ++p) {
-            const int L = __ldg(I.lit + p);
-            const bool neg = L & 1;
-            float tv[VW];
-            ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const float term = neg ? -tv[e] : tv[e];
-                leaf[e] = (in_leaf == 0) ? term : leaf[e] + term;
-                if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
-            }
-            if (++in_leaf == 32) {
-#pragma unroll
-                for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
-                in_leaf = 0;
-            }
-        }
-        if (in_leaf) {
-#pragma unroll
-            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
-        }
-#pragma unroll
-        for (int e = 0; e < VW; ++e) f[e] = lc[e].finish();
     }
 }
 
@@ -440,10 +454,12 @@ cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st
 // consecutive items are packed with shuffles into whole 32-bit words.
 
 template <int VW, int KFIX>
-__global__ void __launch_bounds__(kThreads)
-    k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
-              const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
-              float *__restrict__ fstore, int mode) {
+__device__ __forceinline__ void forward_body(const DevInst &I, const float *__restrict__ t0,
+                                             const float *__restrict__ t1,
+                                             const float *__restrict__ t_ovr, const DevStep &D,
+                                             uint32_t *__restrict__ ubits,
+                                             float *__restrict__ fstore, int mode, int blk,
+                                             int nblk) {
     constexpr int NU = VW <= 4 ? 2 : 1;  // items per lane per iteration
     __shared__ unsigned long long s_w[kThreads];
     __shared__ float s_l[kThreads];
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(kThreads)
     const int g = threadIdx.x % G;
     const int col = g * VW;
     const long long total = (long long)I.m * G;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long stride = (long long)nblk * blockDim.x;
 
     float lacc[VW];
     unsigned long long wacc[VW];
@@ -468,7 +484,7 @@ __global__ void __launch_bounds__(kThreads)
         wacc[e] = 0ull;
     }
     constexpr int LPW = 32 / VW;  // lanes whose bits share one 32-bit word
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+    for (long long base = (long long)blk * blockDim.x + (threadIdx.x & ~31); base < total;
          base += NU * stride) {
         long long item[NU];
         bool act[NU];
@@ -539,7 +555,7 @@ __global__ void __launch_bounds__(kThreads)
     }
 
     // per restart: block sums (one restart slot of the group at a time)
-    unsigned long long *acc = D.wu_acc + (long long)(blockIdx.x % kRep) * B;
+    unsigned long long *acc = D.wu_acc + (long long)(blk % kRep) * B;
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
         s_w[threadIdx.x] = wacc[e];
@@ -554,12 +570,12 @@ __global__ void __launch_bounds__(kThreads)
             }
             const int b = threadIdx.x * VW + e;
             if (sw) atomicAdd(acc + b, sw);
-            D.lpart[(long long)blockIdx.x * B + b] = sl;
+            D.lpart[(long long)blk * B + b] = sl;
         }
         __syncthreads();
     }
     __threadfence();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&D.sc->counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(&D.sc->counter, 1u) == nblk - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -598,6 +614,14 @@ __global__ void __launch_bounds__(kThreads)
             sc->steps_done = steps + 1;
         }
     }
+}
+
+template <int VW, int KFIX>
+__global__ void __launch_bounds__(kThreads)
+    k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
+              const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
+              float *__restrict__ fstore, int mode) {
+    forward_body<VW, KFIX>(I, t0, t1, t_ovr, D, ubits, fstore, mode, blockIdx.x, gridDim.x);
 }
 
 int auto_fwd_vw(int B) { return B < 8 ? B : 8; }
@@ -667,9 +691,9 @@ cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D
 // Per restart b < B, block b of the light kernel also reduces the loss of
 // the evaluated x from the forward block partials.
 
-__device__ __forceinline__ void reduce_loss(const DevStep &D, int B) {
+__device__ __forceinline__ void reduce_loss(const DevStep &D, int B, int blk, int nblk) {
     __shared__ float s_red[kThreads];
-    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    for (int b = blk; b < B; b += nblk) {
         float acc = 0.0f;
         for (int k = threadIdx.x; k < D.fwd_blocks; k += blockDim.x)
             acc += D.lpart[(long long)k * B + b];
@@ -693,9 +717,10 @@ __device__ __forceinline__ void reduce_loss(const DevStep &D, int B) {
 // dyadic tree; the last chunk block of a (variable, group) combines the
 // chunk partials with the same tree and applies the update.
 template <int VW, int KFIX>
-__global__ void __launch_bounds__(kThreads)
-    k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
-                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
+__device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, const DevStep &D,
+                                           int mode, const float *__restrict__ t_ovr,
+                                           const float *__restrict__ gscale,
+                                           float *__restrict__ grad_out, int blk) {
     __shared__ float s_term[kChunk * VW];
     __shared__ int s_last;
     const int B = I.B;
@@ -705,8 +730,8 @@ __global__ void __launch_bounds__(kThreads)
     float *tnext;
     step_buffers(S, D, mode, t_ovr, tcur, tnext);
     const AdamView A = adam_view(D.sc);
-    const int gg = blockIdx.x % G;
-    const long long cidx = blockIdx.x / G;
+    const int gg = blk % G;
+    const long long cidx = blk / G;
     const int col = gg * VW;
     int lo = 0, hi = I.n_heavy - 1;
     while (lo < hi) {
@@ -833,6 +858,13 @@ __global__ void __launch_bounds__(kThreads)
     finish_variable<VW>(S, D, A, mode, q0, col, tcur, Ssum, tnext, gscale, grad_out);
 }
 
+template <int VW, int KFIX>
+__global__ void __launch_bounds__(kThreads)
+    k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
+    heavy_body<VW, KFIX>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x);
+}
+
 // k_backward_light: one block per range of consecutive light variables.
 // Phase 1 spreads the block's (occurrence, group of VS restarts) items over
 // all threads and stages each occurrence term in shared memory (row r of
@@ -840,9 +872,10 @@ __global__ void __launch_bounds__(kThreads)
 // VU restarts) to one thread, which sums its rows in the fixed order and
 // applies the update.
 template <int VS, int VU, int KFIX>
-__global__ void __launch_bounds__(kThreads)
-    k_backward_light(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
-                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
+__device__ __forceinline__ void light_body(const DevInst &I, const DevState &S, const DevStep &D,
+                                           int mode, const float *__restrict__ t_ovr,
+                                           const float *__restrict__ gscale,
+                                           float *__restrict__ grad_out, int blk, int nblk) {
     extern __shared__ float4 dyn_smem[];
     __shared__ int s_voff[kThreads + 1];
     const int B = I.B;
@@ -850,12 +883,12 @@ __global__ void __launch_bounds__(kThreads)
     const float *tcur;
     float *tnext;
     step_buffers(S, D, mode, t_ovr, tcur, tnext);
-    if (mode == BWD_UPDATE) reduce_loss(D, B);
-    if ((int)blockIdx.x >= I.n_lblk) return;  // a grid of one block when every variable is heavy
+    if (mode == BWD_UPDATE) reduce_loss(D, B, blk, nblk);
+    if ((int)blk >= I.n_lblk) return;  // a grid of one block when every variable is heavy
     const AdamView A = adam_view(D.sc);
     const uint32_t *__restrict__ ubits = S.ubits;
     float *sterm = reinterpret_cast<float *>(dyn_smem);
-    const int2 rg = I.lblk[blockIdx.x];
+    const int2 rg = I.lblk[blk];
     const int v0 = rg.x, v1 = rg.y;
     const int nv = v1 - v0;
     for (int r = threadIdx.x; r <= nv; r += kThreads) s_voff[r] = __ldg(I.voff + v0 + r);
@@ -973,6 +1006,13 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <int VS, int VU, int KFIX>
+__global__ void __launch_bounds__(kThreads)
+    k_backward_light(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                     const float *__restrict__ gscale, float *__restrict__ grad_out) {
+    light_body<VS, VU, KFIX>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
+}
+
+template <int VS, int VU, int KFIX>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
                                      int mode, const float *t_ovr, const float *gscale,
                                      float *grad_out, cudaStream_t st) {
@@ -1015,8 +1055,98 @@ cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &
     }
 }
 
+// ------------------------------------------------------------ batched step
+// One launch of each pass advances every instance of a slot table by one
+// iteration of Algorithm 1.  A block finds its slot by binary search in the
+// launch's block prefix table and runs the same body on that slot's views
+// with its block index inside the slot.
+
+__device__ __forceinline__ int slot_of(const int *__restrict__ start, int nslot, int blk) {
+    int lo = 0, hi = nslot - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int VW>
+__global__ void __launch_bounds__(kThreads)
+    k_forward_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
+    const int s = slot_of(start, nslot, blockIdx.x);
+    const int b0 = __ldg(start + s), b1 = __ldg(start + s + 1);
+    const SlotDesc &sd = slots[s];
+    forward_body<VW, 0>(sd.I, sd.S.t0, sd.S.t1, nullptr, sd.D, sd.S.ubits, sd.S.fstore, FWD_STEP,
+                        blockIdx.x - b0, b1 - b0);
+}
+
+template <int VU>
+__global__ void __launch_bounds__(kThreads)
+    k_backward_heavy_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
+    const int s = slot_of(start, nslot, blockIdx.x);
+    const SlotDesc &sd = slots[s];
+    heavy_body<VU, 0>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr,
+                      blockIdx.x - __ldg(start + s));
+}
+
+template <int VS, int VU>
+__global__ void __launch_bounds__(kThreads)
+    k_backward_light_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
+    const int s = slot_of(start, nslot, blockIdx.x);
+    const int b0 = __ldg(start + s), b1 = __ldg(start + s + 1);
+    const SlotDesc &sd = slots[s];
+    light_body<VS, VU, 0>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr, blockIdx.x - b0,
+                          b1 - b0);
+}
+
+int heavy_blocks_of(const DevInst &I) {
+    return I.n_heavy > 0 ? (int)(I.heavy_chunks * (I.B / update_vw(I.B))) : 0;
+}
+
+int light_blocks_of(const DevInst &I) { return I.n_lblk > 0 ? I.n_lblk : 1; }
+
+template <int VS, int VU>
+static cudaError_t launch_batch_bwd(const SlotDesc *slots, int nslot, const int *heavy_start,
+                                    int heavy_total, const int *light_start, int light_total,
+                                    size_t smem, cudaStream_t st) {
+    if (heavy_total > 0) {
+        k_backward_heavy_batch<VU><<<(unsigned)heavy_total, kThreads, 0, st>>>(slots, heavy_start, nslot);
+        const cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    k_backward_light_batch<VS, VU><<<(unsigned)light_total, kThreads, smem, st>>>(slots, light_start, nslot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_start, int fwd_total,
+                              const int *heavy_start, int heavy_total, const int *light_start,
+                              int light_total, int B, int fwd_vw, int stage_vw, int occ_cap,
+                              cudaStream_t st) {
+    if (nslot <= 0) return cudaSuccess;
+    switch (fwd_vw) {
+        case 8: k_forward_batch<8><<<(unsigned)fwd_total, kThreads, 0, st>>>(slots, fwd_start, nslot); break;
+        case 4: k_forward_batch<4><<<(unsigned)fwd_total, kThreads, 0, st>>>(slots, fwd_start, nslot); break;
+        case 2: k_forward_batch<2><<<(unsigned)fwd_total, kThreads, 0, st>>>(slots, fwd_start, nslot); break;
+        default: k_forward_batch<1><<<(unsigned)fwd_total, kThreads, 0, st>>>(slots, fwd_start, nslot); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    const size_t smem = (size_t)occ_cap * B * sizeof(float);
+    const int vu = update_vw(B);
+    switch (stage_vw * 8 + vu) {
+        case 8 * 8 + 4: return launch_batch_bwd<8, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 4 * 8 + 4: return launch_batch_bwd<4, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 2 * 8 + 4: return launch_batch_bwd<2, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 1 * 8 + 4: return launch_batch_bwd<1, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 2 * 8 + 2: return launch_batch_bwd<2, 2>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 1 * 8 + 2: return launch_batch_bwd<1, 2>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        case 1 * 8 + 1: return launch_batch_bwd<1, 1>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // loss per restart from the forward partials (used where no update follows)
-__global__ void k_loss_reduce(DevStep D, int B) { reduce_loss(D, B); }
+__global__ void k_loss_reduce(DevStep D, int B) { reduce_loss(D, B, blockIdx.x, gridDim.x); }
 
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st) {
     const int blocks = B < 152 * 4 ? B : 152 * 4;

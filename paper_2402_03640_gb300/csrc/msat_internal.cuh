@@ -106,6 +106,15 @@ struct DenseDev {
     CUtensorMap tmA, tmB;
 };
 
+// One instance of a batched launch (serving): its device views and the
+// first block of each pass in the launch grids.  start[] tables of the
+// launches are prefix sums of the per-slot block counts.
+struct SlotDesc {
+    DevInst I;
+    DevState S;
+    DevStep D;
+};
+
 // Kernel modes of the variable pass.
 enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
 
@@ -215,6 +224,15 @@ cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &
                             const float *t_override, const float *gscale, float *grad_out,
                             cudaStream_t st);
 cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st);
+// Batched step over nslot instances (all with the same B, variable-length
+// clause path): fwd_start / heavy_start / light_start are device int[nslot+1]
+// block prefixes; totals are the grid sizes.
+cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_start, int fwd_total,
+                              const int *heavy_start, int heavy_total, const int *light_start,
+                              int light_total, int B, int fwd_vw, int stage_vw, int occ_cap,
+                              cudaStream_t st);
+int heavy_blocks_of(const DevInst &I);
+int light_blocks_of(const DevInst &I);
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
                                cudaStream_t st);

@@ -55,6 +55,35 @@ class msat_info(ctypes.Structure):
                 ("uniform_len", ctypes.c_int32)]
 
 
+class msat_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class msat_request(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_int32), ("steps", ctypes.c_int32), ("n_clauses", ctypes.c_int64),
+                ("clause_off", ctypes.c_void_p), ("lits", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("seed_x", ctypes.c_uint64)]
+
+
+class msat_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("best_restart", ctypes.c_int32),
+                ("best_cost", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("n_vars", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class msat_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
+                ("peak_running", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_in_use", ctypes.c_int64), ("hbm_budget", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("graph_captures", ctypes.c_int64)]
+
+
 class msat_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4)]
 
@@ -105,6 +134,14 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_objective_noalloc": ([i32, i64, P, P, P, P, i32, P, P, P], ctypes.c_int),
             "msat_check": ([P], ctypes.c_int),
             "msat_evaluate_x": ([P, i32, P], ctypes.c_int),
+            "msat_server_config_default": ([P], ctypes.c_int),
+            "msat_server_create": ([P, P], ctypes.c_int),
+            "msat_server_destroy": ([P], None),
+            "msat_submit": ([P, P, P], ctypes.c_int),
+            "msat_poll": ([P, ctypes.c_uint64, P, P, P], ctypes.c_int),
+            "msat_wait": ([P, ctypes.c_uint64, ctypes.c_double, P, P, P], ctypes.c_int),
+            "msat_cancel": ([P, ctypes.c_uint64], ctypes.c_int),
+            "msat_server_get_stats": ([P, P], ctypes.c_int),
             "msat_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():

@@ -208,6 +208,92 @@ class Solver:
         return grad
 
 
+class Server:
+    """Continuous-batching request loop (msat_server_*): submit CNF instances
+    at any time, poll or wait for their results."""
+
+    def __init__(self, restarts: int = 8, hbm_budget: int = 0, max_slots: int = 0, chunk: int = 0,
+                 lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        lib = native.load()
+        self._lib = lib
+        cfg = native.msat_server_config()
+        check(lib.msat_server_config_default(ctypes.byref(cfg)))
+        cfg.restarts = int(restarts)
+        cfg.hbm_budget = int(hbm_budget)
+        if max_slots:
+            cfg.max_slots = int(max_slots)
+        if chunk:
+            cfg.chunk = int(chunk)
+        cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
+        self.B = int(restarts)
+        self._srv = ctypes.c_void_p()
+        check(lib.msat_server_create(ctypes.byref(self._srv), ctypes.byref(cfg)))
+        self._n = {}
+
+    def submit(self, cnf, steps: int, seed_x: int = 1) -> int:
+        off = np.ascontiguousarray(cnf.off, dtype=np.int64)
+        lits = np.ascontiguousarray(cnf.lits, dtype=np.int32)
+        w = None if cnf.weights is None else np.ascontiguousarray(cnf.weights, dtype=np.int64)
+        req = native.msat_request(n_vars=int(cnf.n), steps=int(steps), n_clauses=int(off.shape[0] - 1),
+                                  clause_off=off.ctypes.data, lits=lits.ctypes.data if lits.size else None,
+                                  weights=None if w is None else w.ctypes.data, seed_x=int(seed_x))
+        t = ctypes.c_uint64()
+        check(self._lib.msat_submit(self._srv, ctypes.byref(req), ctypes.byref(t)))
+        self._n[t.value] = int(cnf.n)
+        return t.value
+
+    def _result(self, rc, res, best, assign, ticket):
+        if rc == native.MSAT_EAGAIN:
+            return None
+        self._n.pop(ticket, None)
+        check(rc)
+        out = {f: getattr(res, f) for f, _ in res._fields_}
+        out["best_costs"] = best
+        out["assignment"] = assign
+        return out
+
+    def poll(self, ticket: int):
+        """The result dict once done, None while queued or running."""
+        res = native.msat_result()
+        best = np.empty(self.B, np.int64)
+        assign = np.empty(self._n.get(ticket, 1), np.uint8)
+        rc = self._lib.msat_poll(self._srv, ticket, ctypes.byref(res), _p(best), _p(assign))
+        return self._result(rc, res, best, assign, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        res = native.msat_result()
+        best = np.empty(self.B, np.int64)
+        assign = np.empty(self._n.get(ticket, 1), np.uint8)
+        rc = self._lib.msat_wait(self._srv, ticket, float(timeout_s), ctypes.byref(res), _p(best), _p(assign))
+        return self._result(rc, res, best, assign, ticket)
+
+    def cancel(self, ticket: int) -> None:
+        check(self._lib.msat_cancel(self._srv, ticket))
+        self._n.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = native.msat_server_stats()
+        check(self._lib.msat_server_get_stats(self._srv, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_srv", None) is not None and self._srv.value:
+            self._lib.msat_server_destroy(self._srv)
+            self._srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def _make_autograd():
     import torch
 
