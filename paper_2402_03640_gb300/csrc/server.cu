@@ -70,6 +70,7 @@ struct SrvDone {
     msat_result res{};
     std::vector<int64_t> best;
     std::vector<uint8_t> assign;
+    std::string error;  // message of a failed request
 };
 
 enum { ST_QUEUED = 0, ST_RUNNING = 1, ST_DONE = 2, ST_FAILED = 3 };
@@ -151,9 +152,11 @@ void pinned_put(msat_server *S, void *p, size_t cap) {
 }
 
 void finish_failed(msat_server *S, uint64_t ticket, int code, Clock::time_point t_submit) {
+    const std::string msg = msat_last_error();
     std::lock_guard<std::mutex> lk(S->mu);
     SrvDone d;
     d.res.status = code;
+    d.error = msg;
     d.res.latency_ms = ms_between(t_submit, Clock::now());
     S->done[ticket] = std::move(d);
     S->state[ticket] = ST_FAILED;
@@ -539,9 +542,10 @@ static int take_result(msat_server *S, uint64_t ticket, msat_result *out, int64_
         if (best_costs) std::copy(d.best.begin(), d.best.end(), best_costs);
         if (assign01) std::copy(d.assign.begin(), d.assign.end(), assign01);
     }
+    const std::string err = d.error;
     S->done.erase(ticket);
     S->state.erase(it);
-    if (status) return fail(status, "msat_poll: the request failed");
+    if (status) return fail(status, "the request failed: " + err);
     return MSAT_OK;
 }
 
