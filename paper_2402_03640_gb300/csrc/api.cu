@@ -220,7 +220,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
         return fail(MSAT_EINVAL, "msat_create: fwd_blocks >= 0 and light_rows 0 or >= 16");
     // light blocks stage occ_cap occurrence rows of B floats in shared memory;
     // a variable with more occurrences is split into 1024-occurrence chunks
-    int32_t occ_cap = kLightSmem / (int32_t)(sizeof(float) * B);
+    int32_t occ_cap = light_occ_cap(B);
     if (cfg.light_rows > 0) occ_cap = std::min(occ_cap, cfg.light_rows);
     if (cfg.f_mode < MSAT_F_AUTO || cfg.f_mode > MSAT_F_EXPANDED)
         return fail(MSAT_EINVAL, "msat_create: unknown f_mode");

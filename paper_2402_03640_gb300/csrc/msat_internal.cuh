@@ -125,6 +125,12 @@ constexpr int kLightMaxDeg = 512;        // more occurrences than this: heavy va
 constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
 
+// Occurrence rows of B floats that one light block stages in kLightSmem
+// bytes of dynamic shared memory.  The light partition and every launch of
+// the light kernel must use the same value: a block that holds more rows than
+// its launch provides would write past its shared allocation.
+inline int light_occ_cap(int B) { return kLightSmem / (int)(sizeof(float) * B); }
+
 // ------------------------------------------------------- fp32 arithmetic
 // Fixed-order float arithmetic of the step.  Every operation is a single
 // IEEE operation rounded to nearest; fused multiply-adds appear only where

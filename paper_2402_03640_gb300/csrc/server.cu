@@ -209,6 +209,9 @@ int rebuild(msat_server *S) {
     int f = 0, h = 0, l = 0;
     for (int i = 0; i < n; ++i) {
         msat_ctx *c = S->slots[(size_t)i].ctx;
+        if (c->B != S->cfg.restarts || c->I.occ_cap > S->occ_cap || c->I.fwd_vw != S->fwd_vw ||
+            c->I.stage_vw != S->stage_vw)
+            return fail(MSAT_ESTATE, "msat server: an instance's launch shape differs from the slot table's");
         hs[i].I = c->I;
         hs[i].S = c->S;
         hs[i].D = c->D;
@@ -430,7 +433,7 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     S->cfg = cfg;
     S->fwd_vw = auto_fwd_vw(B);
     S->stage_vw = auto_stage_vw(B);
-    S->occ_cap = (kLightSmem - 16) / (int)(sizeof(float) * B);
+    S->occ_cap = light_occ_cap(B);
     const int M = cfg.max_slots + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
     if (!e) e = cudaStreamCreateWithFlags(&S->admit, cudaStreamNonBlocking);
