@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import uniform_ksat, zipf_weighted  # noqa: E402
+from synth import serving_stream, uniform_ksat, zipf_weighted  # noqa: E402
 
 L2_BYTES = 129 * 2 ** 20
 
@@ -47,6 +47,13 @@ WORKLOADS = {
                           "uniform random 3-SAT, n=50, m=215 (seed 0), B=1"),
 }
 DEFAULT_WORKLOAD = "ksat3_n5000_m21500_b256"
+# the request stream of the serving measurement: k in {3,4,5}, n log-uniform
+# in [100, 50000], ratio U[4.0, 4.6] scaled to each k's threshold, Poisson
+# arrivals; each request takes SERVE_STEPS steps with SERVE_RESTARTS restarts
+SERVING = "serving_k345_b8"
+SERVE_STREAM_LEN = 10000
+SERVE_STEPS = 1000
+SERVE_RESTARTS = 8
 # workloads whose step also runs the dense tensor-core evaluation of the rounded batch
 DENSE_EVAL = {"ksat3_n5000_m21500_b256"}
 LR = 1e-4
@@ -154,10 +161,48 @@ def dist_env():
     return ws, rank, local
 
 
+def run_reference_serving(args):
+    """The oracle on the serving stream: each sampled request solved with a
+    reduced step count, its time scaled to the request's full step count
+    (the per-step work of Algorithm 1 is constant)."""
+    from oracle import oracle
+    oracle.build()
+    B, steps, probe = SERVE_RESTARTS, SERVE_STEPS, 10
+    reqs = serving_stream(SERVE_STREAM_LEN, rate_per_s=args.serve_rate, seed=0)
+    budget = 20.0
+    spent, est, used = 0.0, 0.0, 0
+    for r in reqs:
+        if spent > budget:
+            break
+        c = r.instance()
+        t = time.perf_counter()
+        oracle.solve(c, B, r.seed, probe, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+        dt = time.perf_counter() - t
+        spent += dt
+        est += dt * (steps + 1) / (probe + 1)
+        used += 1
+    value = used / est
+    sample = (f"the first {used} requests of the serving stream, {probe} of the {steps} steps each "
+              f"run by the FP32-mode C oracle on one host thread, time scaled by {steps + 1}/{probe + 1}")
+    line = {
+        "impl": "reference", "metric": "instances/s", "value": value, "unit": "instances/s",
+        "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SERVING, "restarts": B, "steps_per_request": steps},
+        "cpu_baseline": {"value": value, "unit": "instances/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == SERVING:
+        return run_reference_serving(args)
     gen, B, desc = WORKLOADS[args.workload]
     cnf = gen()
     from oracle import oracle
@@ -341,6 +386,9 @@ def run_ours(args):
 
     launches = prof["forward"][0] + prof["backward"][0] + prof["evaluate"][0] + prof["other"][0]
     info = solver.info()
+    serving = None
+    if args.workload == DEFAULT_WORKLOAD and args.serve_requests > 0:
+        serving = serve_compare(pkg, args.serve_requests, args.serve_rate)
     _, cost = solver.step(0, want_loss=False)
     dense_ok = None
     if dense:
@@ -369,8 +417,134 @@ def run_ours(args):
         "wall_s_timed": wall1 - wall0,
         "final_cost_min": int(cost.min()),
         "dense_eval_matches_sparse": dense_ok,
+        "serving": serving,
     }
     solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[i]
+
+
+def serve_compare(pkg, count, rate, steps=SERVE_STEPS, B=SERVE_RESTARTS, lr=LR):
+    """The first `count` requests of the serving stream, submitted on their
+    Poisson arrival schedule (a) to the continuous-batching server and (b) to
+    the plain loop that solves one instance at a time (msat_create, msat_step,
+    msat_best, msat_destroy).  Latency runs from a request's arrival to its
+    result on the host; instances/s = requests / (last result - first arrival)."""
+    reqs = serving_stream(SERVE_STREAM_LEN, rate_per_s=rate, seed=0)[:count]
+    cnfs = [r.instance() for r in reqs]
+    warm = uniform_ksat(300, 1290, 3, seed=123)
+
+    def pace(t0, r):
+        d = t0 + r.arrival_s - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+
+    # (a) served
+    with pkg.Server(restarts=B, lr=lr) as srv:
+        srv.wait(srv.submit(warm, 20, seed_x=1))
+        t0 = time.perf_counter()
+        sub, tickets = [], []
+        for r, c in zip(reqs, cnfs):
+            pace(t0, r)
+            sub.append(time.perf_counter())
+            tickets.append(srv.submit(c, steps, seed_x=r.seed))
+        served = [srv.wait(t, 3600.0) for t in tickets]
+        st = srv.stats()
+    done_a = [sub[i] + served[i]["latency_ms"] / 1e3 for i in range(count)]
+    lat_a = [done_a[i] - (t0 + reqs[i].arrival_s) for i in range(count)]
+    span_a = max(done_a) - t0
+
+    # (b) one instance at a time
+    with pkg.Solver.from_cnf(warm, restarts=B, seed_x=1, lr=lr) as s:
+        s.step(20, want_loss=False, want_cost=False)
+    t0 = time.perf_counter()
+    done_b, alone = [], []
+    for r, c in zip(reqs, cnfs):
+        pace(t0, r)
+        with pkg.Solver.from_cnf(c, restarts=B, seed_x=r.seed, lr=lr) as s:
+            s.step(steps, want_loss=False, want_cost=False)
+            _, best = s.best()
+        done_b.append(time.perf_counter())
+        alone.append(best)
+    lat_b = [done_b[i] - (t0 + reqs[i].arrival_s) for i in range(count)]
+    span_b = max(done_b) - t0
+
+    equal = all(np.array_equal(served[i]["best_costs"], alone[i]) for i in range(count))
+    lit_evals = sum(c.nnz for c in cnfs) * B * steps
+    h2d = sum(c.off.nbytes + c.lits.nbytes + (0 if c.weights is None else c.weights.nbytes) for c in cnfs)
+    d2h = sum(B * 8 + c.n for c in cnfs)
+    ks = [r.k for r in reqs]
+    return {
+        "instances_per_s": count / span_a,
+        "p50_ms": 1e3 * _pct(lat_a, 50), "p99_ms": 1e3 * _pct(lat_a, 99),
+        "one_at_a_time": {"instances_per_s": count / span_b, "p50_ms": 1e3 * _pct(lat_b, 50),
+                          "p99_ms": 1e3 * _pct(lat_b, 99)},
+        "speedup_vs_one_at_a_time": span_b / span_a,
+        "final_costs_equal": bool(equal),
+        "mean_best_cost": float(np.mean([x["best_cost"] for x in served])),
+        "served_literal_evals_per_s": lit_evals / span_a,
+        "peak_running": st["peak_running"], "graph_captures": st["graph_captures"],
+        "requests": count, "arrival_rate_per_s": rate, "steps": steps, "restarts": B, "lr": lr,
+        "k_counts": {str(k): ks.count(k) for k in (3, 4, 5)},
+        "n_range": [min(r.n for r in reqs), max(r.n for r in reqs)],
+        "h2d_bytes_per_request": h2d / count, "d2h_bytes_per_request": d2h / count,
+        "sample": f"the first {count} of a {SERVE_STREAM_LEN}-request stream (seed 0): k uniform in "
+                  "{3,4,5}, n log-uniform in [100, 50000], m/n uniform in [4.0, 4.6] scaled by "
+                  "alpha_k/alpha_3, Poisson arrivals",
+    }
+
+
+def run_serving(args):
+    import torch
+    import paper_2402_03640_gb300 as pkg
+    from paper_2402_03640_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    pkg_build.build()
+    pkg.load()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    res = serve_compare(pkg, args.serve_requests, args.serve_rate)
+    clk = clocks.stop()
+    value = res["instances_per_s"]
+    if ws > 1:
+        # every rank serves its own copy of the stream: instances/s add up
+        t = torch.tensor([value], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        value = float(t.item())
+    line = {
+        "metric": "instances/s", "value": value, "unit": "instances/s", "n_gpus": ws,
+        "steps": res["steps"], "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SERVING, "description": res["sample"], "requests": res["requests"],
+                   "arrival_rate_per_s": res["arrival_rate_per_s"], "restarts": res["restarts"],
+                   "steps_per_request": res["steps"], "l2": "working set of the mix larger than L2"},
+        "serving": res, "roofline": None, "cpu_baseline": None, "clocks": clk,
+        "e2e": {"value": value, "unit": "instances/s",
+                "h2d_bytes_per_step": res["h2d_bytes_per_request"],
+                "d2h_bytes_per_step": res["d2h_bytes_per_request"],
+                "note": "requests enter as host arrays through msat_submit and leave through msat_wait"},
+        "gpu_launches": None,
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -395,13 +569,18 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SERVING], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving comparison (0: skip it on the default line)")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="Poisson arrival rate, requests/s")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == SERVING:
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -76,12 +76,15 @@ typedef struct {
                           into 1024-occurrence chunks (0 = automatic)          */
     /* Launch shapes (0 = automatic).  None of them changes a result bit: the
      * order of every sum is fixed by the instance, not by the launch.       */
-    int32_t fwd_vw;     /* restarts per thread in the clause pass (1,2,4,8; <= B) */
+    int32_t fwd_vw;     /* restarts per thread in the clause pass (1,2,4,8;
+                           <= B and >= B/256)                                   */
     int32_t stage_vw;   /* restarts per thread staging occurrence terms
-                           (1,2,4,8,16; <= B)                                   */
+                           (1,2,4,8,16; <= B and >= B/256)                      */
     int32_t fwd_blocks; /* thread blocks of the clause pass                    */
-    int32_t light_rows; /* occurrence rows a light block stages in shared
-                           memory (>= 16)                                       */
+    int32_t light_rows; /* leaf tasks of one light-variable block, a task
+                           being one 32-occurrence leaf of a variable for
+                           stage_vw restarts (>= 16; light_rows x stage_vw x 4
+                           bytes <= 48 KiB; 0 = 512)                            */
     int32_t reserved1;
 } msat_config;
 

@@ -216,24 +216,30 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     const int32_t stage_vw = cfg.stage_vw ? cfg.stage_vw : auto_stage_vw(B);
     if (!pow2_le(fwd_vw, std::min(8, B)) || !pow2_le(stage_vw, std::min(16, B)))
         return fail(MSAT_EINVAL, "msat_create: fwd_vw / stage_vw must be powers of two <= min(8 or 16, B)");
+    if ((int64_t)fwd_vw * kThreads < B || (int64_t)stage_vw * kThreads < B)
+        return fail(MSAT_EINVAL, "msat_create: B / fwd_vw and B / stage_vw must not exceed 256");
     if (cfg.fwd_blocks < 0 || cfg.light_rows < 0 || (cfg.light_rows > 0 && cfg.light_rows < 16))
         return fail(MSAT_EINVAL, "msat_create: fwd_blocks >= 0 and light_rows 0 or >= 16");
-    // light blocks stage occ_cap occurrence rows of B floats in shared memory;
-    // a variable with more occurrences is split into 1024-occurrence chunks
-    int32_t occ_cap = light_occ_cap(B);
-    if (cfg.light_rows > 0) occ_cap = std::min(occ_cap, cfg.light_rows);
+    // a light block holds at most task_cap leaf tasks (32-occurrence leaf x
+    // group of stage_vw restarts); a variable with more leaves than fit is
+    // split into 1024-occurrence chunks instead (heavy variable)
+    const int32_t GS = B / stage_vw;
+    int32_t task_cap = cfg.light_rows > 0 ? cfg.light_rows : kTaskCap;
+    task_cap = std::max(task_cap, GS);
+    if (light_smem_bytes(task_cap, stage_vw) > 48 * 1024)
+        return fail(MSAT_EINVAL, "msat_create: light_rows x stage_vw x 4 bytes exceeds 48 KiB");
     if (cfg.f_mode < MSAT_F_AUTO || cfg.f_mode > MSAT_F_EXPANDED)
         return fail(MSAT_EINVAL, "msat_create: unknown f_mode");
     if (cfg.f_mode == MSAT_F_EXPANDED && (kfix != 3 || m >= (1LL << 28)))
         return fail(MSAT_EINVAL, "msat_create: MSAT_F_EXPANDED needs every clause to have 3 literals");
     if (cfg.heavy_deg < 0) return fail(MSAT_EINVAL, "msat_create: heavy_deg < 0");
-    const int32_t heavy_deg = cfg.heavy_deg > 0 ? std::min(cfg.heavy_deg, std::min(occ_cap, kLightMaxDeg))
-                                                : std::min(occ_cap, kLightMaxDeg);
+    const int32_t leaf_room = 32 * (task_cap / GS);  // occurrences of the longest light variable
+    const int32_t heavy_deg = std::min(cfg.heavy_deg > 0 ? cfg.heavy_deg : kLightMaxDeg,
+                                       std::min(leaf_room, kLightMaxDeg));
     std::vector<int32_t> hvar, hchunk0(1, 0);
     std::vector<int2> lblk;
     {
-        const int32_t vmax = kThreads / G;
-        int32_t v0 = -1, cnt = 0, occ_in = 0;
+        int32_t v0 = -1, cnt = 0, tasks_in = 0;
         for (int32_t i = 0; i < n_vars; ++i) {
             const int32_t d = voff[(size_t)i + 1] - voff[(size_t)i];
             if (d > heavy_deg) {
@@ -243,17 +249,18 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
                 v0 = -1;
                 continue;
             }
-            if (v0 >= 0 && (cnt == vmax || occ_in + d > occ_cap)) {
+            const int32_t tasks = std::max(1, (d + 31) / 32) * GS;
+            if (v0 >= 0 && (cnt == kThreads || tasks_in + tasks > task_cap)) {
                 lblk.push_back(make_int2(v0, i));
                 v0 = -1;
             }
             if (v0 < 0) {
                 v0 = i;
                 cnt = 0;
-                occ_in = 0;
+                tasks_in = 0;
             }
             ++cnt;
-            occ_in += d;
+            tasks_in += tasks;
         }
         if (v0 >= 0) lblk.push_back(make_int2(v0, n_vars));
     }
@@ -355,7 +362,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     I.occ_shift = expand ? 3 : 1;
     I.occx = d_occx;
     I.n_lblk = (int32_t)lblk.size();
-    I.occ_cap = occ_cap;
+    I.task_cap = task_cap;
     I.fwd_vw = fwd_vw;
     I.stage_vw = stage_vw;
     I.lblk = d_lblk;

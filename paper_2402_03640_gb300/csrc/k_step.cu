@@ -126,45 +126,34 @@ __device__ __forceinline__ void clause_range(const DevInst &I, int kfix, int j, 
     }
 }
 
-// f_j and sat of a clause longer than 32 literals: 32-literal leaves in
-// order, combined by the dyadic counter.  Kept out of line so its counter
-// registers do not weigh on the common short-clause path.
-template <int VW, bool WANT_SAT>
-__device__ __noinline__ void clause_value_long(const DevInst &I, const float *__restrict__ t,
-                                               int beg, int end, int col, float (&f)[VW],
-                                               bool (&sat)[VW]) {
-    const int B = I.B;
-    LeafCounter<6> lc[VW];
-    float leaf[VW];
+// Dyadic counter of finished 32-literal leaves for clauses longer than 32
+// literals (the same binary counter as LeafCounter), on a per-thread array
+// indexed at run time: it lives in local memory and is touched once per 32
+// literals, so short clauses never use it.
+template <int VW>
+__device__ __forceinline__ void leaf_push(float (&stk)[6][VW], unsigned &cnt, float (&v)[VW]) {
+    unsigned c = cnt;
+    int lvl = 0;
+    while (c & 1u) {
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-        lc[e].init();
-        sat[e] = false;
-    }
-    int in_leaf = 0;
-    for (int p = beg; p < end; ++p) {
-        const int L = __ldg(I.lit + p);
-        const bool neg = L & 1;
-        float tv[VW];
-        ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const float term = neg ? -tv[e] : tv[e];
-            leaf[e] = (in_leaf == 0) ? term : leaf[e] + term;
-            if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
-        }
-        if (++in_leaf == 32) {
-#pragma unroll
-            for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
-            in_leaf = 0;
-        }
-    }
-    if (in_leaf) {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) lc[e].push(leaf[e]);
+        for (int e = 0; e < VW; ++e) v[e] = stk[lvl][e] + v[e];
+        c >>= 1;
+        ++lvl;
     }
 #pragma unroll
-    for (int e = 0; e < VW; ++e) f[e] = lc[e].finish();
+    for (int e = 0; e < VW; ++e) stk[lvl][e] = v[e];
+    ++cnt;
+}
+
+template <int VW>
+__device__ __forceinline__ void leaf_finish(const float (&stk)[6][VW], unsigned cnt, float (&r)[VW]) {
+    bool have = false;
+    for (int lvl = 0; lvl < 6; ++lvl) {
+        if (!((cnt >> lvl) & 1u)) continue;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) r[e] = have ? (stk[lvl][e] + r[e]) : stk[lvl][e];
+        have = true;
+    }
 }
 
 // f_j for VW restarts in the fixed order (literal order, 32-literal leaves,
@@ -174,16 +163,20 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
                                              int beg, int end, int col, float (&f)[VW],
                                              bool (&sat)[VW]) {
     const int B = I.B;
-    if (end - beg > 32) {
-        clause_value_long<VW, WANT_SAT>(I, t, beg, end, col, f, sat);
-        return;
-    }
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
         f[e] = 0.0f;
         sat[e] = false;
     }
+    float stk[6][VW];
+    unsigned nleaf = 0;
+    int in_leaf = 0;
+#pragma unroll 2
     for (int p = beg; p < end; ++p) {
+        if (in_leaf == 32) {
+            leaf_push<VW>(stk, nleaf, f);
+            in_leaf = 0;
+        }
         const int L = __ldg(I.lit + p);
         const bool neg = L & 1;
         float tv[VW];
@@ -191,9 +184,14 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const float term = neg ? -tv[e] : tv[e];
-            f[e] = (p == beg) ? term : f[e] + term;
+            f[e] = (in_leaf == 0) ? term : f[e] + term;
             if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
         }
+        ++in_leaf;
+    }
+    if (nleaf) {  // more than 32 literals: the last leaf, then the counter
+        leaf_push<VW>(stk, nleaf, f);
+        leaf_finish<VW>(stk, nleaf, f);
     }
 }
 
@@ -241,21 +239,15 @@ __device__ __forceinline__ const uint32_t *ubits_word(const DevInst &I, const ui
 }
 
 // f_j for VW restarts (col .. col+VW-1) of the clause of occurrence word o
-// (clause j in the bits above occ_shift, literal sign in bit 0).  f comes
-// from the clause pass's store when there is one; otherwise it is
-// recomputed in the literal order, for 3-literal clauses from the expanded
-// occurrence record (position of the variable in bits 1-2 of o, the other
-// two literals in ox; own_var is the occurring variable).
+// (clause j in the bits above occ_shift, literal sign in bit 0), recomputed
+// in the literal order; for 3-literal clauses from the expanded occurrence
+// record (position of the variable in bits 1-2 of o, the other two
+// literals in ox; own_var is the occurring variable).
 template <int VW, int KFIX>
 __device__ __forceinline__ void fetch_f(const DevInst &I, int kfix, const float *__restrict__ t,
-                                        const float *__restrict__ fstore, int o, int2 ox,
-                                        int own_var, int col, float (&f)[VW]) {
+                                        int o, int2 ox, int own_var, int col, float (&f)[VW]) {
     const int B = I.B;
     const int j = o >> I.occ_shift;
-    if (fstore) {
-        ldv<VW>(fstore + (int64_t)j * B + col, f);
-        return;
-    }
     bool sat[VW];
     if constexpr (KFIX == 3) {
         if (I.occx) {
@@ -303,6 +295,116 @@ __device__ __forceinline__ void term_from_f(const DevInst &I, int o, uint32_t ni
         if ((nib >> e) & 1u) {
             const float g = (wj * f[e]) * cs[e];
             term[e] = neg ? -g : g;
+        }
+    }
+}
+
+// Terms of C occurrences (words o, expanded records ox, valid where ok) of
+// variable own_var for VW restarts at col, all loads of the C occurrences in
+// flight together.  With the clause pass's store, q = (float)w_j * f_j (NaN
+// where satisfied) gives the term +-(q * 2/W_U) or +0; otherwise the unsat
+// bits select the restarts whose f is recomputed (fetched together with the
+// bits when unsat clauses are dense).
+template <int VW, int KFIX, int C, bool STORE>
+__device__ __forceinline__ void occ_terms(const DevInst &I, const DevState &S, int kfix,
+                                          const float *__restrict__ tcur, const int (&o)[C],
+                                          const int2 (&ox)[C], const bool (&ok)[C], int own_var,
+                                          int col, const float (&cs)[VW], bool dense,
+                                          float (&term)[C][VW]) {
+    const int B = I.B;
+    if constexpr (STORE) {
+        float q[C][VW];
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            if (ok[u]) {
+                ldv<VW>(S.fstore + (int64_t)(o[u] >> I.occ_shift) * B + col, q[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) q[u][e] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            const bool neg = o[u] & 1;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const float g = q[u][e] * cs[e];
+                term[u][e] = (q[u][e] != q[u][e]) ? 0.0f : (neg ? -g : g);
+            }
+        }
+    } else {
+        uint32_t wd[C];
+        float f[C][VW];
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            wd[u] = ok[u] ? __ldg(ubits_word(I, S.ubits, o[u], col)) : 0u;
+            if (dense && ok[u]) fetch_f<VW, KFIX>(I, kfix, tcur, o[u], ox[u], own_var, col, f[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            const uint32_t nib = ok[u] ? occ_nib<VW>(I, o[u], wd[u], col) : 0u;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) term[u][e] = 0.0f;
+            if (nib) {
+                if (!dense) fetch_f<VW, KFIX>(I, kfix, tcur, o[u], ox[u], own_var, col, f[u]);
+                term_from_f<VW>(I, o[u], nib, f[u], cs, term[u]);
+            }
+        }
+    }
+}
+
+// The same terms of C consecutive occurrences of one leaf, added in order
+// to the leaf sum (first: the chunk opens the leaf, so its first term
+// starts the sum instead of being added to +0).
+template <int VW, int KFIX, int C, bool STORE>
+__device__ __forceinline__ void occ_accumulate(const DevInst &I, const DevState &S, int kfix,
+                                               const float *__restrict__ tcur, const int (&o)[C],
+                                               const int2 (&ox)[C], const bool (&ok)[C],
+                                               int own_var, int col, const float (&cs)[VW],
+                                               bool dense, bool first, float (&leaf)[VW]) {
+    const int B = I.B;
+    float v[C][VW];
+    if constexpr (STORE) {
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            if (ok[u]) {
+                ldv<VW>(S.fstore + (int64_t)(o[u] >> I.occ_shift) * B + col, v[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) v[u][e] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            if (!ok[u]) continue;
+            const bool neg = o[u] & 1;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const float g = v[u][e] * cs[e];
+                const float term = (v[u][e] != v[u][e]) ? 0.0f : (neg ? -g : g);
+                leaf[e] = (first && u == 0) ? term : leaf[e] + term;
+            }
+        }
+    } else {
+        uint32_t wd[C];
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            wd[u] = ok[u] ? __ldg(ubits_word(I, S.ubits, o[u], col)) : 0u;
+            if (dense && ok[u]) fetch_f<VW, KFIX>(I, kfix, tcur, o[u], ox[u], own_var, col, v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            if (!ok[u]) continue;
+            const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
+            float term[VW];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) term[e] = 0.0f;
+            if (nib) {
+                if (!dense) fetch_f<VW, KFIX>(I, kfix, tcur, o[u], ox[u], own_var, col, v[u]);
+                term_from_f<VW>(I, o[u], nib, v[u], cs, term);
+            }
+#pragma unroll
+            for (int e = 0; e < VW; ++e) leaf[e] = (first && u == 0) ? term[e] : leaf[e] + term[e];
         }
     }
 }
@@ -356,6 +458,16 @@ __device__ __forceinline__ void finish_variable(const DevState &S, const DevStep
                                                 const float (&Ssum)[VW], float *tnext,
                                                 const float *__restrict__ gscale,
                                                 float *__restrict__ grad_out) {
+    if constexpr (VW > 4) {  // slices of four restarts keep the live registers down
+#pragma unroll
+        for (int h = 0; h < VW; h += 4) {
+            float part[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) part[e] = Ssum[h + e];
+            finish_variable<4>(S, D, A, mode, q0 + h, col + h, tcur, part, tnext, gscale, grad_out);
+        }
+        return;
+    }
     float tv[VW], gr[VW];
     ldv<VW>(tcur + q0, tv);
 #pragma unroll
@@ -537,36 +649,54 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
             if (act[h]) {
                 const long long wj = I.w ? __ldg(I.w + jj[h]) : 1ll;
                 const float wf = (float)wj;
+                float q[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
+                    q[e] = __int_as_float(0x7fc00000);  // satisfied: NaN marker
                     if (!sat[h][e]) {
                         nib |= 1u << e;
                         wacc[e] += (unsigned long long)wj;
-                        lacc[e] += (wf * f[h][e]) * f[h][e];
+                        q[e] = wf * f[h][e];
+                        lacc[e] += q[e] * f[h][e];
                     }
                 }
-                if (fstore) stv<VW>(fstore + (int64_t)jj[h] * B + col, f[h]);
+                if (fstore) stv<VW>(fstore + (int64_t)jj[h] * B + col, q);
             }
-            unsigned word = nib << ((lane % LPW) * VW);
+            if (!fstore) {  // uniform: the variable pass reads the bits only when f is recomputed
+                unsigned word = nib << ((lane % LPW) * VW);
 #pragma unroll
-            for (int o = 1; o < LPW; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-            if (act[h] && (lane % LPW) == 0) ubits[(item[h] * VW) >> 5] = word;
+                for (int o = 1; o < LPW; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
+                if (act[h] && (lane % LPW) == 0) ubits[(item[h] * VW) >> 5] = word;
+            }
         }
     }
 
-    // per restart: block sums (one restart slot of the group at a time)
+    // per restart: block sums.  The threads of restart group g are those
+    // with threadIdx.x % G == g (G divides the block).  Lanes of one warp in
+    // the same group are combined by xor shuffles, then thread g adds the
+    // blockDim / max(G, 32) partials of its group.  The weights are integers
+    // (any order is exact); the loss partial's order is free because the
+    // loss is reported and never fed back into x.
     unsigned long long *acc = D.wu_acc + (long long)(blk % kRep) * B;
+    const int per_group = blockDim.x / (G < 32 ? 32 : G);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
-        s_w[threadIdx.x] = wacc[e];
-        s_l[threadIdx.x] = lacc[e];
+        unsigned long long sw = wacc[e];
+        float sl = lacc[e];
+        for (int o = G; o < 32; o <<= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        }
+        s_w[threadIdx.x] = sw;
+        s_l[threadIdx.x] = sl;
         __syncthreads();
         if (threadIdx.x < G) {
-            unsigned long long sw = 0;
-            float sl = 0.0f;
-            for (int r = threadIdx.x; r < blockDim.x; r += G) {
-                sw += s_w[r];
-                sl += s_l[r];
+            sw = 0;
+            sl = 0.0f;
+            const int step = G < 32 ? 32 : G;
+            for (int k = 0; k < per_group; ++k) {
+                sw += s_w[threadIdx.x + k * step];
+                sl += s_l[threadIdx.x + k * step];
             }
             const int b = threadIdx.x * VW + e;
             if (sw) atomicAdd(acc + b, sw);
@@ -617,7 +747,7 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
 }
 
 template <int VW, int KFIX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
               const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
               float *__restrict__ fstore, int mode) {
@@ -625,7 +755,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 int auto_fwd_vw(int B) { return B < 8 ? B : 8; }
-int auto_stage_vw(int B) { return B < 8 ? B : 8; }
+int auto_stage_vw(int B) { return B < 4 ? B : 4; }
 int update_vw(int B) { return B < 4 ? B : 4; }
 
 template <int VW>
@@ -716,7 +846,7 @@ __device__ __forceinline__ void reduce_loss(const DevStep &D, int B, int blk, in
 // memory; 32 leaves of 32 terms are summed in order and combined by the
 // dyadic tree; the last chunk block of a (variable, group) combines the
 // chunk partials with the same tree and applies the update.
-template <int VW, int KFIX>
+template <int VW, int KFIX, bool STORE>
 __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, const DevStep &D,
                                            int mode, const float *__restrict__ t_ovr,
                                            const float *__restrict__ gscale,
@@ -752,41 +882,27 @@ __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, 
     for (int e = 0; e < VW; ++e) cs[e] = D.cscale[col + e];
 
     if (mode != BWD_BITS_ONLY) {
-        // phase 1: the chunk's terms into shared memory, four per thread in
-        // flight; when unsat clauses are dense, f is fetched together with
-        // the unsat words instead of after them
+        // phase 1: the chunk's terms into shared memory, four per thread in flight
         const bool dense = D.sc->dense != 0;
         const bool expanded = KFIX == 3 && I.occx != nullptr;
         int o[4];
         int2 ox[4];
-        uint32_t wd[4];
-        float f[4][VW];
+        bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
-            o[u] = r < cn ? __ldcs(I.occ + cb + r) : 0;
-            ox[u] = (expanded && r < cn) ? __ldcs(I.occx + cb + r) : make_int2(0, 0);
+            ok[u] = r < cn;
+            o[u] = ok[u] ? __ldcs(I.occ + cb + r) : 0;
+            ox[u] = (expanded && ok[u]) ? __ldcs(I.occx + cb + r) : make_int2(0, 0);
         }
+        float term[4][VW];
+        occ_terms<VW, KFIX, 4, STORE>(I, S, kfix, tcur, o, ox, ok, i, col, cs, dense, term);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = threadIdx.x + u * kThreads;
-            wd[u] = r < cn ? __ldg(ubits_word(I, S.ubits, o[u], col)) : 0u;
-            if (dense && r < cn) fetch_f<VW, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], i, col, f[u]);
-        }
+            if (ok[u]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = threadIdx.x + u * kThreads;
-            if (r < cn) {
-                float term[VW];
-#pragma unroll
-                for (int e = 0; e < VW; ++e) term[e] = 0.0f;
-                const uint32_t nib = occ_nib<VW>(I, o[u], wd[u], col);
-                if (nib) {
-                    if (!dense) fetch_f<VW, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], i, col, f[u]);
-                    term_from_f<VW>(I, o[u], nib, f[u], cs, term);
-                }
-#pragma unroll
-                for (int e = 0; e < VW; ++e) s_term[r * VW + e] = term[e];
+                for (int e = 0; e < VW; ++e) s_term[r * VW + e] = term[u][e];
             }
         }
         __syncthreads();
@@ -858,175 +974,176 @@ __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, 
     finish_variable<VW>(S, D, A, mode, q0, col, tcur, Ssum, tnext, gscale, grad_out);
 }
 
-template <int VW, int KFIX>
+template <int VW, int KFIX, bool STORE>
 __global__ void __launch_bounds__(kThreads)
     k_backward_heavy(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
                      const float *__restrict__ gscale, float *__restrict__ grad_out) {
-    heavy_body<VW, KFIX>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x);
+    heavy_body<VW, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x);
 }
 
 // k_backward_light: one block per range of consecutive light variables.
-// Phase 1 spreads the block's (occurrence, group of VS restarts) items over
-// all threads and stages each occurrence term in shared memory (row r of
-// the block's occurrences, B floats); phase 2 gives each (variable, group of
-// VU restarts) to one thread, which sums its rows in the fixed order and
-// applies the update.
-template <int VS, int VU, int KFIX>
-__device__ __forceinline__ void light_body(const DevInst &I, const DevState &S, const DevStep &D,
-                                           int mode, const float *__restrict__ t_ovr,
-                                           const float *__restrict__ gscale,
-                                           float *__restrict__ grad_out, int blk, int nblk) {
+// A task is (variable, 32-occurrence leaf, group of VS restarts); the
+// restart group is the fastest index, so the lanes of a warp that share a
+// leaf read consecutive columns of the same rows.  A thread sums its leaf's
+// terms in the stored order, with the loads of four occurrences in flight
+// at a time.  A variable with one leaf (or none) is finished by the same
+// thread; the leaves of a longer variable meet in shared memory and the
+// thread of its first leaf combines them by the dyadic counter, then
+// applies the update.  A thread keeps its restart group for all its tasks
+// (the task stride, kThreads, is a multiple of the group count).
+template <int VS, int KFIX, bool STORE>
+__device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, const DevStep &D,
+                                          int mode, const float *__restrict__ t_ovr,
+                                          const float *__restrict__ gscale,
+                                          float *__restrict__ grad_out, int blk, int nblk) {
+    constexpr int C = 4;  // occurrences in flight per thread
     extern __shared__ float4 dyn_smem[];
     __shared__ int s_voff[kThreads + 1];
+    __shared__ int s_lpre[kThreads + 1];
+    __shared__ int s_wtot[kThreads / 32];
     const int B = I.B;
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
     const float *tcur;
     float *tnext;
     step_buffers(S, D, mode, t_ovr, tcur, tnext);
     if (mode == BWD_UPDATE) reduce_loss(D, B, blk, nblk);
-    if ((int)blk >= I.n_lblk) return;  // a grid of one block when every variable is heavy
+    if (blk >= I.n_lblk) return;  // a grid of one block when every variable is heavy
     const AdamView A = adam_view(D.sc);
-    const uint32_t *__restrict__ ubits = S.ubits;
-    float *sterm = reinterpret_cast<float *>(dyn_smem);
+    float *s_leaf = reinterpret_cast<float *>(dyn_smem);
     const int2 rg = I.lblk[blk];
-    const int v0 = rg.x, v1 = rg.y;
-    const int nv = v1 - v0;
-    for (int r = threadIdx.x; r <= nv; r += kThreads) s_voff[r] = __ldg(I.voff + v0 + r);
+    const int v0 = rg.x, nv = rg.y - rg.x;  // nv <= kThreads
+
+    // occurrence offsets and leaf counts of the block's variables, then the
+    // exclusive prefix of the leaf counts (warp scans, then warp totals)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int nl = 0;
+    if (threadIdx.x < nv) {
+        const int a = __ldg(I.voff + v0 + threadIdx.x);
+        const int b = __ldg(I.voff + v0 + threadIdx.x + 1);
+        s_voff[threadIdx.x] = a;
+        if (threadIdx.x == nv - 1) s_voff[nv] = b;
+        nl = mode == BWD_BITS_ONLY ? 1 : max(1, (b - a + 31) >> 5);
+    }
+    int inc = nl;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_wtot[warp] = inc;
     __syncthreads();
-    const int s0 = s_voff[0];
-    const int nocc = s_voff[nv] - s0;
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) before += w < warp ? s_wtot[w] : 0;
+    if (threadIdx.x < nv) s_lpre[threadIdx.x] = before + inc - nl;
+    if (threadIdx.x == nv - 1) s_lpre[nv] = before + inc;
+    __syncthreads();
 
-    if (mode != BWD_BITS_ONLY) {
-        // phase 1: occurrence terms into shared memory, four items per thread in flight
-        const int GS = B / VS;
-        const int sshift = __ffs(GS) - 1;  // GS is a power of two
-        const int colS = (threadIdx.x & (GS - 1)) * VS;
-        float cs[VS];
+    const int GS = B / VS;
+    const int gshift = __ffs(GS) - 1;  // GS is a power of two <= kThreads
+    const int col = (threadIdx.x & (GS - 1)) * VS;
+    const int nleaves = s_lpre[nv];
+    const int ntasks = nleaves << gshift;
+    float cs[VS];
 #pragma unroll
-        for (int e = 0; e < VS; ++e) cs[e] = D.cscale[colS + e];
-        const int items = nocc << sshift;
-        // NB items per thread in flight; when unsat clauses are dense, f is
-        // fetched together with the unsat words instead of after them
-        constexpr int NB = VS <= 4 ? 4 : 2;
-        const bool dense = D.sc->dense != 0;
-        const bool expanded = KFIX == 3 && I.occx != nullptr;
-        for (int base = threadIdx.x; base < items; base += NB * kThreads) {
-            int o[NB], own[NB];
-            int2 ox[NB];
-            uint32_t wd[NB];
-            float f[NB][VS];
-#pragma unroll
-            for (int u = 0; u < NB; ++u) {
-                const int it = base + u * kThreads;
-                const int r = it >> sshift;
-                o[u] = it < items ? __ldcs(I.occ + s0 + r) : 0;
-                ox[u] = (expanded && it < items) ? __ldcs(I.occx + s0 + r) : make_int2(0, 0);
-                own[u] = 0;
-                if (expanded) {
-                    // variable owning local occurrence r: last v with s_voff[v] - s0 <= r
-                    int lo = 0, hi = nv - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_voff[mid] - s0 <= r) lo = mid; else hi = mid - 1;
-                    }
-                    own[u] = v0 + lo;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < NB; ++u) {
-                const int it = base + u * kThreads;
-                wd[u] = it < items ? __ldg(ubits_word(I, ubits, o[u], colS)) : 0u;
-                if (dense && it < items)
-                    fetch_f<VS, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], own[u], colS, f[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < NB; ++u) {
-                const int it = base + u * kThreads;
-                if (it < items) {
-                    const int r = it >> sshift;
-                    float term[VS];
-#pragma unroll
-                    for (int e = 0; e < VS; ++e) term[e] = 0.0f;
-                    const uint32_t nib = occ_nib<VS>(I, o[u], wd[u], colS);
-                    if (nib) {
-                        if (!dense) fetch_f<VS, KFIX>(I, kfix, tcur, S.fstore, o[u], ox[u], own[u], colS, f[u]);
-                        term_from_f<VS>(I, o[u], nib, f[u], cs, term);
-                    }
-                    stv<VS>(sterm + (int64_t)r * B + colS, term);
-                }
-            }
+    for (int e = 0; e < VS; ++e) cs[e] = D.cscale[col + e];
+    const bool dense = D.sc->dense != 0;
+    const bool expanded = KFIX == 3 && I.occx != nullptr;
+
+    for (int t = threadIdx.x; t < ntasks; t += kThreads) {
+        const int ti = t >> gshift;
+        int lo = 0, hi = nv - 1;  // the variable: last vloc with s_lpre[vloc] <= ti
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_lpre[mid] <= ti) lo = mid; else hi = mid - 1;
         }
-        __syncthreads();
-    }
-
-    // phase 2: one thread per (variable, restart group)
-    const int GU = B / VU;
-    const int ushift = __ffs(GU) - 1;
-    const int colU = (threadIdx.x & (GU - 1)) * VU;
-    const int vloc = threadIdx.x >> ushift;
-    if (vloc >= nv) return;
-    const int i = v0 + vloc;
-    const int64_t q0 = (int64_t)i * B + colU;
-    if (mode == BWD_BITS_ONLY) {
-        float xv[VU];
-        ldv_rw<VU>(S.x + q0, xv);
+        const int vloc = lo;
+        const int L = ti - s_lpre[vloc];
+        const int nleaf = s_lpre[vloc + 1] - s_lpre[vloc];
+        const int i = v0 + vloc;
+        const int64_t q0 = (int64_t)i * B + col;
+        if (mode == BWD_BITS_ONLY) {
+            float xv[VS];
+            ldv_rw<VS>(S.x + q0, xv);
 #pragma unroll
-        for (int e = 0; e < VU; ++e)
-            if (D.improved[colU + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
-        return;
-    }
-    const int rb = s_voff[vloc] - s0, re = s_voff[vloc + 1] - s0;
-    LeafCounter<5> lc[VU];  // at most kLightMaxDeg = 512 rows: 16 leaves
-    float leaf[VU];
+            for (int e = 0; e < VS; ++e)
+                if (D.improved[col + e]) S.bestx[q0 + e] = xv[e] > 0.0f;
+            continue;
+        }
+        const int pb = s_voff[vloc] + 32 * L;
+        const int pe = min(pb + 32, s_voff[vloc + 1]);
+        float leaf[VS];
 #pragma unroll
-    for (int e = 0; e < VU; ++e) {
-        lc[e].init();
-        leaf[e] = 0.0f;
-    }
-    int in_leaf = 0;
-    for (int r = rb; r < re; ++r) {
-        float term[VU];
-        ldv_rw<VU>(sterm + (int64_t)r * B + colU, term);
+        for (int e = 0; e < VS; ++e) leaf[e] = 0.0f;
+        for (int p = pb; p < pe; p += C) {
+            int o[C];
+            int2 ox[C];
+            bool ok[C];
 #pragma unroll
-        for (int e = 0; e < VU; ++e) leaf[e] = (in_leaf == 0) ? term[e] : leaf[e] + term[e];
-        if (++in_leaf == 32) {
-#pragma unroll
-            for (int e = 0; e < VU; ++e) lc[e].push(leaf[e]);
-            in_leaf = 0;
+            for (int u = 0; u < C; ++u) {
+                ok[u] = p + u < pe;
+                o[u] = ok[u] ? __ldcs(I.occ + p + u) : 0;
+                ox[u] = (expanded && ok[u]) ? __ldcs(I.occx + p + u) : make_int2(0, 0);
+            }
+            occ_accumulate<VS, KFIX, C, STORE>(I, S, kfix, tcur, o, ox, ok, i, col, cs, dense, p == pb, leaf);
+        }
+        if (nleaf == 1) {
+            finish_variable<VS>(S, D, A, mode, q0, col, tcur, leaf, tnext, gscale, grad_out);
+        } else {
+            stv<VS>(s_leaf + (int64_t)ti * B + col, leaf);
         }
     }
-    if (in_leaf) {
+    if (mode == BWD_BITS_ONLY || nleaves == nv) return;  // uniform: no variable has two leaves
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntasks; t += kThreads) {
+        const int ti = t >> gshift;
+        int lo = 0, hi = nv - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_lpre[mid] <= ti) lo = mid; else hi = mid - 1;
+        }
+        const int vloc = lo;
+        const int nleaf = s_lpre[vloc + 1] - s_lpre[vloc];
+        if (ti != s_lpre[vloc] || nleaf == 1) continue;
+        LeafCounter<5> lc[VS];  // at most kLightMaxDeg = 512 occurrences: 16 leaves
 #pragma unroll
-        for (int e = 0; e < VU; ++e) lc[e].push(leaf[e]);
+        for (int e = 0; e < VS; ++e) lc[e].init();
+        for (int l = 0; l < nleaf; ++l) {
+            float v[VS];
+            ldv_rw<VS>(s_leaf + (int64_t)(ti + l) * B + col, v);
+#pragma unroll
+            for (int e = 0; e < VS; ++e) lc[e].push(v[e]);
+        }
+        float Ssum[VS];
+#pragma unroll
+        for (int e = 0; e < VS; ++e) Ssum[e] = lc[e].finish();
+        const int64_t q0 = (int64_t)(v0 + vloc) * B + col;
+        finish_variable<VS>(S, D, A, mode, q0, col, tcur, Ssum, tnext, gscale, grad_out);
     }
-    float Ssum[VU];
-#pragma unroll
-    for (int e = 0; e < VU; ++e) Ssum[e] = lc[e].finish();
-    finish_variable<VU>(S, D, A, mode, q0, colU, tcur, Ssum, tnext, gscale, grad_out);
 }
 
-template <int VS, int VU, int KFIX>
+template <int VS, int KFIX, bool STORE>
 __global__ void __launch_bounds__(kThreads)
     k_backward_light(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
                      const float *__restrict__ gscale, float *__restrict__ grad_out) {
-    light_body<VS, VU, KFIX>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
+    vars_body<VS, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
 }
 
-template <int VS, int VU, int KFIX>
+template <int VS, int VU, int KFIX, bool STORE>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
                                      int mode, const float *t_ovr, const float *gscale,
                                      float *grad_out, cudaStream_t st) {
     if (I.n_heavy > 0) {
         const long long hblocks = I.heavy_chunks * (I.B / VU);  // one block per (chunk, group)
-        k_backward_heavy<VU, KFIX><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
-                                                                            gscale, grad_out);
+        k_backward_heavy<VU, KFIX, STORE><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
+                                                                                   gscale, grad_out);
         const cudaError_t e = cudaGetLastError();
         if (e) return e;
     }
     const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
-    const size_t smem = (size_t)I.occ_cap * I.B * sizeof(float);
-    k_backward_light<VS, VU, KFIX><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
-                                                                               gscale, grad_out);
+    const size_t smem = light_smem_bytes(I.task_cap, VS);
+    k_backward_light<VS, KFIX, STORE><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
+                                                                                 gscale, grad_out);
     return cudaGetLastError();
 }
 
@@ -1034,8 +1151,13 @@ template <int VS, int VU>
 static cudaError_t launch_backward_vw(const DevInst &I, const DevState &S, const DevStep &D,
                                       int mode, const float *t_ovr, const float *gscale,
                                       float *grad_out, cudaStream_t st) {
-    if (I.kfix == 3) return launch_backward_k<VS, VU, 3>(I, S, D, mode, t_ovr, gscale, grad_out, st);
-    return launch_backward_k<VS, VU, 0>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    // f stored by the clause pass, or recomputed from the unsat bits
+    if (S.fstore) {
+        if (I.kfix == 3) return launch_backward_k<VS, VU, 3, true>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+        return launch_backward_k<VS, VU, 0, true>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    }
+    if (I.kfix == 3) return launch_backward_k<VS, VU, 3, false>(I, S, D, mode, t_ovr, gscale, grad_out, st);
+    return launch_backward_k<VS, VU, 0, false>(I, S, D, mode, t_ovr, gscale, grad_out, st);
 }
 
 cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
@@ -1071,7 +1193,7 @@ __device__ __forceinline__ int slot_of(const int *__restrict__ start, int nslot,
 }
 
 template <int VW>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_forward_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
     const int s = slot_of(start, nslot, blockIdx.x);
     const int b0 = __ldg(start + s), b1 = __ldg(start + s + 1);
@@ -1085,18 +1207,17 @@ __global__ void __launch_bounds__(kThreads)
     k_backward_heavy_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
     const int s = slot_of(start, nslot, blockIdx.x);
     const SlotDesc &sd = slots[s];
-    heavy_body<VU, 0>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr,
+    heavy_body<VU, 0, true>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr,
                       blockIdx.x - __ldg(start + s));
 }
 
-template <int VS, int VU>
+template <int VS>
 __global__ void __launch_bounds__(kThreads)
     k_backward_light_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
     const int s = slot_of(start, nslot, blockIdx.x);
     const int b0 = __ldg(start + s), b1 = __ldg(start + s + 1);
     const SlotDesc &sd = slots[s];
-    light_body<VS, VU, 0>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr, blockIdx.x - b0,
-                          b1 - b0);
+    vars_body<VS, 0, true>(sd.I, sd.S, sd.D, BWD_UPDATE, nullptr, nullptr, nullptr, blockIdx.x - b0, b1 - b0);
 }
 
 int heavy_blocks_of(const DevInst &I) {
@@ -1114,13 +1235,13 @@ static cudaError_t launch_batch_bwd(const SlotDesc *slots, int nslot, const int 
         const cudaError_t e = cudaGetLastError();
         if (e) return e;
     }
-    k_backward_light_batch<VS, VU><<<(unsigned)light_total, kThreads, smem, st>>>(slots, light_start, nslot);
+    k_backward_light_batch<VS><<<(unsigned)light_total, kThreads, smem, st>>>(slots, light_start, nslot);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_start, int fwd_total,
                               const int *heavy_start, int heavy_total, const int *light_start,
-                              int light_total, int B, int fwd_vw, int stage_vw, int occ_cap,
+                              int light_total, int B, int fwd_vw, int stage_vw, int task_cap,
                               cudaStream_t st) {
     if (nslot <= 0) return cudaSuccess;
     switch (fwd_vw) {
@@ -1131,9 +1252,10 @@ cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_s
     }
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    const size_t smem = (size_t)occ_cap * B * sizeof(float);
+    const size_t smem = light_smem_bytes(task_cap, stage_vw);
     const int vu = update_vw(B);
     switch (stage_vw * 8 + vu) {
+        case 16 * 8 + 4: return launch_batch_bwd<16, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
         case 8 * 8 + 4: return launch_batch_bwd<8, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
         case 4 * 8 + 4: return launch_batch_bwd<4, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);
         case 2 * 8 + 4: return launch_batch_bwd<2, 4>(slots, nslot, heavy_start, heavy_total, light_start, light_total, smem, st);

@@ -48,9 +48,10 @@ struct DevInst {
                                   // bits 1-2 hold the variable's position in its clause)
     const int2 *occx;             // [nnz] other two literals of a 3-literal clause, or nullptr
     int32_t n_lblk;               // blocks of the light-variable pass
-    int32_t occ_cap;              // occurrence rows one light block stages in shared memory
+    int32_t task_cap;             // leaf tasks (32-occurrence leaf x restart group) of
+                                  // one light block; sizes its shared leaf partials
     int32_t fwd_vw;               // restarts per thread in the clause pass
-    int32_t stage_vw;             // restarts per thread staging occurrence terms
+    int32_t stage_vw;             // restarts per thread of a light-variable leaf task
     const int2 *lblk;             // [n_lblk] variable range [x, y) of each light block
 };
 
@@ -88,7 +89,9 @@ struct DevState {
     float *t0, *t1;        // double-buffered tanh(x), [n][B]
     uint32_t *ubits;       // unsat bits, flat index j*B + b
     uint8_t *bestx;        // [n][B] best assignment (0/1)
-    float *fstore;         // [m][B] f of the last clause pass, or nullptr: recompute f
+    float *fstore;         // [m][B] of the last clause pass: (float)w_j * f_j where clause
+                           // j is unsat for restart b, NaN where it is satisfied; or
+                           // nullptr: the variable pass recomputes f from the unsat bits
 };
 
 // Dense tensor-core evaluation (k_dense.cu): e4m3 clause matrix W^T
@@ -120,16 +123,17 @@ enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
 
 constexpr int kThreads = 256;
 constexpr int kRep = 32;                 // replicas of the per-restart cost accumulator
-constexpr int kLightSmem = 40 * 1024;    // shared memory of one light block (term rows)
-constexpr int kLightMaxDeg = 512;        // more occurrences than this: heavy variable
+constexpr int kTaskCap = 512;          // default leaf tasks of one light block
+constexpr int kLightMaxDeg = 512;      // more occurrences than this: heavy variable
 constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
 
-// Occurrence rows of B floats that one light block stages in kLightSmem
-// bytes of dynamic shared memory.  The light partition and every launch of
-// the light kernel must use the same value: a block that holds more rows than
-// its launch provides would write past its shared allocation.
-inline int light_occ_cap(int B) { return kLightSmem / (int)(sizeof(float) * B); }
+// Shared memory of a light block: the partial sums of its leaf tasks
+// (task_cap x stage_vw floats).  Every launch of the light kernel must use
+// the task cap of the partition its blocks were built with.
+inline size_t light_smem_bytes(int task_cap, int stage_vw) {
+    return (size_t)task_cap * (size_t)stage_vw * sizeof(float);
+}
 
 // ------------------------------------------------------- fp32 arithmetic
 // Fixed-order float arithmetic of the step.  Every operation is a single
@@ -230,12 +234,12 @@ cudaError_t launch_backward(const DevInst &I, const DevState &S, const DevStep &
                             const float *t_override, const float *gscale, float *grad_out,
                             cudaStream_t st);
 cudaError_t launch_tanh(const float *x, float *t, int64_t count, cudaStream_t st);
-// Batched step over nslot instances (all with the same B, variable-length
-// clause path): fwd_start / heavy_start / light_start are device int[nslot+1]
+// Batched step over nslot instances (all with the same B and launch shape,
+// f stored by the clause pass; variable-length clause path): fwd_start / heavy_start / light_start are device int[nslot+1]
 // block prefixes; totals are the grid sizes.
 cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_start, int fwd_total,
                               const int *heavy_start, int heavy_total, const int *light_start,
-                              int light_total, int B, int fwd_vw, int stage_vw, int occ_cap,
+                              int light_total, int B, int fwd_vw, int stage_vw, int task_cap,
                               cudaStream_t st);
 int heavy_blocks_of(const DevInst &I);
 int light_blocks_of(const DevInst &I);

@@ -111,7 +111,7 @@ struct msat_server {
     cudaEvent_t round_ev[2] = {nullptr, nullptr};
     bool round_pending[2] = {false, false};
     int round_idx = 0;
-    int fwd_vw = 0, stage_vw = 0, occ_cap = 0;
+    int fwd_vw = 0, stage_vw = 0, task_cap = 0;
     // pinned result buffers are reused (freeing pinned memory synchronises the device)
     std::multimap<size_t, void *> pinned_free;
 };
@@ -209,8 +209,8 @@ int rebuild(msat_server *S) {
     int f = 0, h = 0, l = 0;
     for (int i = 0; i < n; ++i) {
         msat_ctx *c = S->slots[(size_t)i].ctx;
-        if (c->B != S->cfg.restarts || c->I.occ_cap > S->occ_cap || c->I.fwd_vw != S->fwd_vw ||
-            c->I.stage_vw != S->stage_vw)
+        if (c->B != S->cfg.restarts || c->I.task_cap != S->task_cap || c->I.fwd_vw != S->fwd_vw ||
+            c->I.stage_vw != S->stage_vw || !c->S.fstore)
             return fail(MSAT_ESTATE, "msat server: an instance's launch shape differs from the slot table's");
         hs[i].I = c->I;
         hs[i].S = c->S;
@@ -243,7 +243,7 @@ int rebuild(msat_server *S) {
         if (!e) {
             const cudaError_t le = launch_step_batch(S->d_slots, n, S->d_starts, f, S->d_starts + M, h,
                                                      S->d_starts + 2 * M, l, S->cfg.restarts, S->fwd_vw,
-                                                     S->stage_vw, S->occ_cap, S->compute);
+                                                     S->stage_vw, S->task_cap, S->compute);
             e = cudaStreamEndCapture(S->compute, &g);
             if (!e) e = le;
         }
@@ -433,7 +433,7 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     S->cfg = cfg;
     S->fwd_vw = auto_fwd_vw(B);
     S->stage_vw = auto_stage_vw(B);
-    S->occ_cap = light_occ_cap(B);
+    S->task_cap = std::max(kTaskCap, B / S->stage_vw);
     const int M = cfg.max_slots + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
     if (!e) e = cudaStreamCreateWithFlags(&S->admit, cudaStreamNonBlocking);

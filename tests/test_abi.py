@@ -55,11 +55,13 @@ def test_config_default(lib):
         (1e-4, 0.9, 0.999, 1e-8, 1, 1)
 
 
-def _create(lib, n, off, lits, w=None, restarts=1):
+def _create(lib, n, off, lits, w=None, restarts=1, **shape):
     from paper_2402_03640_gb300 import native
     cfg = native.msat_config()
     lib.msat_config_default(ctypes.byref(cfg))
     cfg.restarts = restarts
+    for k, v in shape.items():
+        setattr(cfg, k, v)
     ctx = ctypes.c_void_p()
     off = np.ascontiguousarray(off, np.int64)
     lits = np.ascontiguousarray(lits, np.int32)
@@ -78,6 +80,9 @@ def _create(lib, n, off, lits, w=None, restarts=1):
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=3), "power of two"),
     (dict(n=0, off=[0], lits=[1]), "n_vars"),
     (dict(n=2000, off=[0, 1030], lits=list(range(1, 1031))), "limit 1024"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], restarts=1024, fwd_vw=2), "must not exceed 256"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], restarts=512, stage_vw=1), "must not exceed 256"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], restarts=4, fwd_vw=8), "powers of two"),
 ])
 def test_create_rejects_malformed_input(lib, case, needle):
     from paper_2402_03640_gb300 import native
