@@ -67,7 +67,8 @@ typedef struct {
     double eps;       /* Adam epsilon (default 1e-8)                           */
     int32_t restarts; /* B: 1, 2, 4, ..., 1024 (a power of two)                */
     int32_t f_mode;   /* how the variable pass gets f_j of unsat clauses:
-                         MSAT_F_AUTO, MSAT_F_STORE (the clause pass stores f),
+                         MSAT_F_AUTO (store unless m x B x 4 bytes > 8 GiB),
+                         MSAT_F_STORE (the clause pass stores w_j f_j),
                          MSAT_F_RECOMPUTE (recomputed from the clause CSR),
                          MSAT_F_EXPANDED (3-literal clauses: recomputed from
                          occurrence records holding the other two literals) */
@@ -84,7 +85,7 @@ typedef struct {
     int32_t light_rows; /* leaf tasks of one light-variable block, a task
                            being one 32-occurrence leaf of a variable for
                            stage_vw restarts (>= 16; light_rows x stage_vw x 4
-                           bytes <= 48 KiB; 0 = 512)                            */
+                           bytes <= 48 KiB; 0 = 256)                            */
     int32_t reserved1;
 } msat_config;
 

@@ -264,9 +264,12 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
         }
         if (v0 >= 0) lblk.push_back(make_int2(v0, n_vars));
     }
-    // f of the clause pass is kept when the [m][B] array is small; otherwise
-    // the variable pass recomputes f of unsatisfied clauses
-    const bool auto_store = (double)m * B * sizeof(float) <= 96.0 * (1 << 20) || B <= 2;
+    // f of the clause pass is kept (as w*f of unsat clauses) unless the [m][B]
+    // array exceeds 8 GiB; otherwise the variable pass recomputes f
+    // the stored w*f costs one [m][B] write and one row gather per
+    // occurrence; recomputing gathers the unsat bits and every literal's row
+    // of t, which measured slower even when the store does not fit in L2
+    const bool auto_store = (double)m * B * sizeof(float) <= 8.0 * (1 << 30) || B <= 2;
     const bool use_fstore = cfg.f_mode == MSAT_F_STORE || (cfg.f_mode == MSAT_F_AUTO && auto_store);
     // recomputing f of 3-literal clauses reads the other two literals from an
     // expanded occurrence record streamed with the occurrence list

@@ -747,7 +747,7 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
 }
 
 template <int VW, int KFIX>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads)
     k_forward(DevInst I, const float *__restrict__ t0, const float *__restrict__ t1,
               const float *__restrict__ t_ovr, DevStep D, uint32_t *__restrict__ ubits,
               float *__restrict__ fstore, int mode) {
@@ -1193,7 +1193,7 @@ __device__ __forceinline__ int slot_of(const int *__restrict__ start, int nslot,
 }
 
 template <int VW>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads)
     k_forward_batch(const SlotDesc *__restrict__ slots, const int *__restrict__ start, int nslot) {
     const int s = slot_of(start, nslot, blockIdx.x);
     const int b0 = __ldg(start + s), b1 = __ldg(start + s + 1);

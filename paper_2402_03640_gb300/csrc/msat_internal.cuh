@@ -123,7 +123,7 @@ enum { BWD_UPDATE = 0, BWD_BITS_ONLY = 1, BWD_GRAD_ONLY = 2 };
 
 constexpr int kThreads = 256;
 constexpr int kRep = 32;                 // replicas of the per-restart cost accumulator
-constexpr int kTaskCap = 512;          // default leaf tasks of one light block
+constexpr int kTaskCap = 256;          // default leaf tasks of one light block
 constexpr int kLightMaxDeg = 512;      // more occurrences than this: heavy variable
 constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
