@@ -86,8 +86,19 @@ typedef struct {
                            being one 32-occurrence leaf of a variable for
                            stage_vw restarts (>= 16; light_rows x stage_vw x 4
                            bytes <= 48 KiB; 0 = 256)                            */
-    int32_t reserved1;
+    int32_t loss_norm;  /* MSAT_LOSS_MEAN_UNSAT (default), MSAT_LOSS_SUM_UNSAT
+                           or MSAT_LOSS_MEAN_ALL; see below                    */
 } msat_config;
+
+/* Normaliser N of the loss L = sum_{j in U} w_j f_j^2 / N and of its
+ * gradient (g_j = 2 w_j f_j / N).  Sec. 4 takes the MSE of f against zero
+ * over the unsatisfied clauses: N = sum_{j in U} w_j (MEAN_UNSAT, the
+ * default).  SUM_UNSAT (N = 1) and MEAN_ALL (N = sum of all weights) are the
+ * two other readings, kept for the ablation; Adam is nearly invariant to a
+ * per-step scale, so they differ mainly through epsilon. */
+#define MSAT_LOSS_MEAN_UNSAT 0
+#define MSAT_LOSS_SUM_UNSAT 1
+#define MSAT_LOSS_MEAN_ALL 2
 
 #define MSAT_F_AUTO 0
 #define MSAT_F_STORE 1
@@ -142,11 +153,64 @@ int msat_step(msat_ctx *ctx, int32_t n_steps, float *loss_out, int64_t *cost_out
  * msat_step with flags.  MSAT_STEP_NO_FINAL_EVAL skips the evaluation of
  * the final x; cost_out then holds the cost of the last x evaluated inside
  * the loop (the x before the last update) and loss_out its loss.  With
- * n_steps = 0 and this flag nothing runs.
+ * n_steps = 0 and this flag nothing runs.  MSAT_STEP_GRAPH replays the
+ * steps from CUDA graphs of one and of 32 steps, captured on the first such
+ * call (on a private stream, so the context stream may be the default
+ * stream); the results are bit for bit those of the plain launches.  It is
+ * ignored while kernel timing (msat_profile_enable) is on.  A graph holds
+ * the context's device pointers; it is released with the context.
  */
 #define MSAT_STEP_NO_FINAL_EVAL 1u
+#define MSAT_STEP_GRAPH 2u
 int msat_step_ex(msat_ctx *ctx, int32_t n_steps, uint32_t flags, float *loss_out,
                  int64_t *cost_out);
+
+/*
+ * Time-limited solving: Algorithm 1 with its wall-clock limit T (Sec. 4,
+ * Algorithm 1 input "time limit"; the loop ends at zero cost or when T is
+ * reached).  Runs the steps in chunks of `chunk` steps (CUDA-graph replays
+ * unless kernel timing is on) until some restart's best cost is 0,
+ * max_steps steps have run, or time_limit_s seconds have passed (checked
+ * after each chunk, so a chunk in flight completes); then evaluates the
+ * final x once, exactly as msat_step does.  The result after k steps is bit
+ * for bit that of msat_step(ctx, k, ...); read it with msat_best.
+ *   steps_out, elapsed_out    steps taken and seconds spent (nullable)
+ *   trace_cost, trace_time    host buffers of trace_cap entries (nullable
+ *                             when trace_cap is 0): after each chunk, and
+ *                             after the final evaluation, the best cost over
+ *                             all restarts and the seconds since the call began
+ *   trace_len                 entries written (nullable)
+ * Synchronous.  EINVAL on a NULL ctx, max_steps < 0, chunk < 1, a negative
+ * time limit or missing trace buffers; ECUDA on a CUDA failure.
+ */
+int msat_solve(msat_ctx *ctx, int64_t max_steps, double time_limit_s, int32_t chunk,
+               int64_t *steps_out, double *elapsed_out, int64_t *trace_cost, double *trace_time,
+               int32_t trace_cap, int32_t *trace_len);
+
+/*
+ * Launch-shape autotuner (no counterpart in the paper: it tunes this
+ * library's kernels).  The launch shapes -- fwd_vw, stage_vw and light_rows
+ * of msat_config -- never change a result bit, so the tuner only times: for
+ * each candidate it creates a scratch context for the instance on `stream`
+ * (same arguments as msat_create), runs 2 warm-up steps and times n_steps
+ * steps with CUDA events, one parameter at a time (stage_vw, then
+ * light_rows, then fwd_vw), starting from the automatic shape.  cfg_out
+ * receives cfg_in (NULL: defaults) with the fastest shape filled in; pass it
+ * to msat_create.  entries (nullable, cap entries) and n_entries report the
+ * candidates timed.  The winner is cached for the process per instance
+ * shape (device, n, m, nnz, restarts, f_mode, weighted, heavy_deg); a cached
+ * call times nothing and reports no entries.  Synchronous; needs memory for
+ * one more context of the instance.  Errors: as msat_create (EINVAL for a
+ * malformed instance or config, ENOMEM), ECUDA on a device failure.
+ */
+typedef struct {
+    int32_t fwd_vw, stage_vw, light_rows;
+    float ms_per_step;
+} msat_tune_entry;
+int msat_autotune(int32_t n_vars, int64_t n_clauses, const int64_t *clause_off,
+                  const int32_t *lits, const int64_t *weights, const msat_config *cfg_in,
+                  void *stream, int32_t n_steps, msat_config *cfg_out, msat_tune_entry *entries,
+                  int32_t cap, int32_t *n_entries);
 
 /*
  * Exact cost of a batch of assignments (Sec. 4, "Unsatisfiable Cores": a

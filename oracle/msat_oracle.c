@@ -37,7 +37,8 @@
  *         in stored order, 32-term leaves summed left to right, leaves
  *         combined by the dyadic tree (split at the largest power of two
  *         below the leaf count).
- *       - g_j = ((float)w_j * f_j) * (2 / (float)W_U) for unsat j, else 0.
+ *       - g_j = ((float)w_j * f_j) * (2 / (float)N) for unsat j, else 0,
+ *         N = W_U unless another normaliser is selected (orc_set_loss_norm).
  *       - grad_i = S_i * fmaf(-t_i, t_i, 1) with S_i the occurrence sum of
  *         +-g_j.
  *       - Adam per element: m = b1*m + (1-b1)*g; v = b2*v + ((1-b2)*g)*g;
@@ -298,6 +299,40 @@ int orc_cost(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, cons
     return ORC_OK;
 }
 
+/* ------------------------------------------------- loss normaliser */
+
+/* Normaliser N of L = sum_{j in U} w_j f_j^2 / N and g_j = 2 w_j f_j / N.
+ * Sec. 4 takes the MSE of f against zero over the unsatisfied clauses, read
+ * as N = W_U = sum_{j in U} w_j (mode 0, the default).  Mode 1 (N = 1, the
+ * sum) and mode 2 (N = total weight, the mean over all clauses) are the
+ * other readings, for the ablation.  Set by orc_set_loss_norm. */
+static int g_loss_norm = 0;
+
+int orc_set_loss_norm(int32_t mode)
+{
+    if (mode < 0 || mode > 2) return ORC_EINVAL;
+    g_loss_norm = mode;
+    return ORC_OK;
+}
+
+static int64_t total_weight(const ocnf *c)
+{
+    int64_t s = 0;
+    for (int64_t j = 0; j < c->m; ++j) s += c->w[j];
+    return s;
+}
+
+/* N in double (FP64 mode) and in float (FP32-canon: (float) of the integer) */
+static double norm_f64(int64_t wu, int64_t wsum)
+{
+    return g_loss_norm == 1 ? 1.0 : (double)(g_loss_norm == 2 ? wsum : wu);
+}
+
+static float norm_f32(int64_t wu, int64_t wsum)
+{
+    return g_loss_norm == 1 ? 1.0f : (float)(g_loss_norm == 2 ? wsum : wu);
+}
+
 /* ------------------------------------------------------ FP64 objective */
 
 /* One evaluation of the relaxed objective at x (double, [n][B]):
@@ -308,6 +343,7 @@ static void objective_f64(const ocnf *c, int32_t B, const double *x, double *f_o
                           double *t, double *f, uint8_t *u)
 {
     const int32_t n = c->n;
+    const int64_t wsum = total_weight(c);
     for (int64_t q = 0; q < (int64_t)n * B; ++q) t[q] = tanh(x[q]);
     for (int32_t b = 0; b < B; ++b) {
         int64_t wu = 0;
@@ -328,14 +364,14 @@ static void objective_f64(const ocnf *c, int32_t B, const double *x, double *f_o
             }
         }
         cost[b] = wu;
-        loss[b] = wu > 0 ? num / (double)wu : 0.0;
+        loss[b] = wu > 0 ? num / norm_f64(wu, wsum) : 0.0;
         if (grad) {
             for (int32_t i = 0; i < n; ++i) grad[(int64_t)i * B + b] = 0.0;
             if (wu > 0) {
-                /* dL/dt_i = sum over unsat j containing i of sign * 2 w_j f_j / W_U */
+                /* dL/dt_i = sum over unsat j containing i of sign * 2 w_j f_j / N */
                 for (int64_t j = 0; j < c->m; ++j) {
                     if (!u[j * B + b]) continue;
-                    double g = 2.0 * (double)c->w[j] * f[j * B + b] / (double)wu;
+                    double g = 2.0 * (double)c->w[j] * f[j * B + b] / norm_f64(wu, wsum);
                     for (int64_t r = c->off[j]; r < c->off[j + 1]; ++r) {
                         int64_t q = (int64_t)c->var[r] * B + b;
                         grad[q] += c->neg[r] ? -g : g;
@@ -419,6 +455,7 @@ static void objective_f32(const ocnf *c, int32_t B, const float *x, work32 *wk, 
                           double *loss, float *grad)
 {
     const int32_t n = c->n;
+    const int64_t wsum = total_weight(c);
     for (int64_t q = 0; q < (int64_t)n * B; ++q) wk->t[q] = orc_tanh32(x[q]);
     for (int32_t b = 0; b < B; ++b) {
         int64_t wu = 0;
@@ -441,9 +478,9 @@ static void objective_f32(const ocnf *c, int32_t B, const float *x, work32 *wk, 
             }
         }
         cost[b] = wu;
-        loss[b] = wu > 0 ? num / (double)wu : 0.0;
+        loss[b] = wu > 0 ? num / norm_f64(wu, wsum) : 0.0;
         if (!grad) continue;
-        float cb = wu > 0 ? 2.0f / (float)wu : 0.0f;
+        float cb = wu > 0 ? 2.0f / norm_f32(wu, wsum) : 0.0f;
         for (int64_t j = 0; j < c->m; ++j)
             wk->g[j * B + b] = wk->u[j * B + b] ? ((float)c->w[j] * wk->f[j * B + b]) * cb : 0.0f;
         for (int32_t i = 0; i < n; ++i) {

@@ -67,8 +67,9 @@ def _load():
                                    i32, P, P, P, P, P]
         lib.orc_solve.argtypes = [i32, i64, P, P, P, i32, u64, f64, f64, f64, f64, i32, i32,
                                   P, P, P, P, P]
+        lib.orc_set_loss_norm.argtypes = [i32]
         for name in ("orc_init_x", "orc_cost", "orc_objective_f64", "orc_objective_f32",
-                     "orc_step32", "orc_solve"):
+                     "orc_step32", "orc_solve", "orc_set_loss_norm"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -83,6 +84,24 @@ def _cnf_arrays(cnf):
     lits = np.ascontiguousarray(cnf.lits, dtype=np.int32)
     w = None if cnf.weights is None else np.ascontiguousarray(cnf.weights, dtype=np.int64)
     return off, lits, w
+
+
+LOSS_NORMS = {"mean_unsat": 0, "sum_unsat": 1, "mean_all": 2}
+
+
+class _loss_norm:
+    """Select the loss normaliser of the oracle for one call (Sec. 4 reading:
+    mean over the unsat clauses; the sum and the mean over all clauses are the
+    ablation's alternatives), restoring the default afterwards."""
+
+    def __init__(self, name):
+        self.mode = LOSS_NORMS[name]
+
+    def __enter__(self):
+        _check(_load().orc_set_loss_norm(self.mode), "set_loss_norm")
+
+    def __exit__(self, *exc):
+        _load().orc_set_loss_norm(0)
 
 
 def _check(rc, what):
@@ -128,7 +147,7 @@ def cost(cnf, assign01: np.ndarray) -> np.ndarray:
     return out
 
 
-def objective_f64(cnf, x: np.ndarray, want_f=False, want_grad=True):
+def objective_f64(cnf, x: np.ndarray, want_f=False, want_grad=True, loss_norm="mean_unsat"):
     """f, unsat mask, cost, loss and gradient at x (double, [n][B]); Sec. 4."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     if x.ndim == 1:
@@ -140,12 +159,13 @@ def objective_f64(cnf, x: np.ndarray, want_f=False, want_grad=True):
     loss = np.empty(B, dtype=np.float64)
     g = np.empty((n, B), dtype=np.float64) if want_grad else None
     off, lits, w = _cnf_arrays(cnf)
-    _check(_load().orc_objective_f64(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(f),
-                                     _p(u), _p(c), _p(loss), _p(g)), "objective_f64")
+    with _loss_norm(loss_norm):
+        _check(_load().orc_objective_f64(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(f),
+                                         _p(u), _p(c), _p(loss), _p(g)), "objective_f64")
     return dict(f=f, unsat=u, cost=c, loss=loss, grad=g)
 
 
-def objective_f32(cnf, x: np.ndarray, want_f=False, want_grad=True):
+def objective_f32(cnf, x: np.ndarray, want_f=False, want_grad=True, loss_norm="mean_unsat"):
     """Same as objective_f64 in the FP32-canon arithmetic."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     if x.ndim == 1:
@@ -157,13 +177,14 @@ def objective_f32(cnf, x: np.ndarray, want_f=False, want_grad=True):
     loss = np.empty(B, dtype=np.float64)
     g = np.empty((n, B), dtype=np.float32) if want_grad else None
     off, lits, w = _cnf_arrays(cnf)
-    _check(_load().orc_objective_f32(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(f),
-                                     _p(u), _p(c), _p(loss), _p(g)), "objective_f32")
+    with _loss_norm(loss_norm):
+        _check(_load().orc_objective_f32(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(f),
+                                         _p(u), _p(c), _p(loss), _p(g)), "objective_f32")
     return dict(f=f, unsat=u, cost=c, loss=loss, grad=g)
 
 
 def step32(cnf, x, mom, vel, steps_done, best_cost, best_assign=None, update=True,
-           lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+           lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, loss_norm="mean_unsat"):
     """One iteration of Algorithm 1 in FP32-canon arithmetic, in place on
     float32 [n][B] arrays x, mom, vel and on best_cost [B] / best_assign [B][n].
     Returns (cost [B], loss [B], grad [n][B] or None)."""
@@ -177,14 +198,15 @@ def step32(cnf, x, mom, vel, steps_done, best_cost, best_assign=None, update=Tru
     loss = np.empty(B, dtype=np.float64)
     g = np.empty((n, B), dtype=np.float32) if update else None
     off, lits, w = _cnf_arrays(cnf)
-    _check(_load().orc_step32(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(mom), _p(vel),
-                              int(steps_done), lr, beta1, beta2, eps, int(bool(update)),
-                              _p(best_cost), _p(best_assign), _p(c), _p(loss), _p(g)), "step32")
+    with _loss_norm(loss_norm):
+        _check(_load().orc_step32(cnf.n, cnf.m, _p(off), _p(lits), _p(w), B, _p(x), _p(mom),
+                                  _p(vel), int(steps_done), lr, beta1, beta2, eps, int(bool(update)),
+                                  _p(best_cost), _p(best_assign), _p(c), _p(loss), _p(g)), "step32")
     return c, loss, g
 
 
 def solve(cnf, B: int, seed_x: int, steps: int, mode: int = MODE_F32, lr=1e-4, beta1=0.9,
-          beta2=0.999, eps=1e-8, want_hist=True, want_x=True):
+          beta2=0.999, eps=1e-8, want_hist=True, want_x=True, loss_norm="mean_unsat"):
     """Algorithm 1 with `steps` optimizer steps (in place of the time limit T)
     and a final evaluation of x_steps.  Returns a dict of numpy arrays."""
     n = cnf.n
@@ -194,6 +216,7 @@ def solve(cnf, B: int, seed_x: int, steps: int, mode: int = MODE_F32, lr=1e-4, b
     ba = np.zeros((B, n), dtype=np.uint8)
     xf = np.empty((n, B), dtype=np.float64) if want_x else None
     off, lits, w = _cnf_arrays(cnf)
-    _check(_load().orc_solve(n, cnf.m, _p(off), _p(lits), _p(w), B, seed_x, lr, beta1, beta2, eps,
-                             steps, mode, _p(ch), _p(lh), _p(best), _p(ba), _p(xf)), "solve")
+    with _loss_norm(loss_norm):
+        _check(_load().orc_solve(n, cnf.m, _p(off), _p(lits), _p(w), B, seed_x, lr, beta1, beta2,
+                                 eps, steps, mode, _p(ch), _p(lh), _p(best), _p(ba), _p(xf)), "solve")
     return dict(cost_hist=ch, loss_hist=lh, best_cost=best, best_assign=ba, x_final=xf)

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -80,6 +81,9 @@ static int dalloc_t(msat_ctx *c, T **p, size_t count) {
 }
 
 static void free_all(msat_ctx *c) {
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->graphK) cudaGraphExecDestroy(c->graphK);
+    c->graph1 = c->graphK = nullptr;
     for (void *p : c->allocs) {
         if (c->pool_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
     }
@@ -233,6 +237,8 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (cfg.f_mode == MSAT_F_EXPANDED && (kfix != 3 || m >= (1LL << 28)))
         return fail(MSAT_EINVAL, "msat_create: MSAT_F_EXPANDED needs every clause to have 3 literals");
     if (cfg.heavy_deg < 0) return fail(MSAT_EINVAL, "msat_create: heavy_deg < 0");
+    if (cfg.loss_norm < MSAT_LOSS_MEAN_UNSAT || cfg.loss_norm > MSAT_LOSS_MEAN_ALL)
+        return fail(MSAT_EINVAL, "msat_create: unknown loss_norm");
     const int32_t leaf_room = 32 * (task_cap / GS);  // occurrences of the longest light variable
     const int32_t heavy_deg = std::min(cfg.heavy_deg > 0 ? cfg.heavy_deg : kLightMaxDeg,
                                        std::min(leaf_room, kLightMaxDeg));
@@ -405,6 +411,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     sc.epsf = (float)cfg.eps;
     sc.dense = 1;
     sc.wsum = wsum;
+    sc.loss_norm = cfg.loss_norm;
     std::vector<long long> best((size_t)B, (long long)wsum);
     cudaError_t e = cudaSuccess;
     if (!e) e = up(d_coff, coff.data(), sizeof(int32_t) * coff.size());
@@ -470,13 +477,45 @@ static cudaError_t eval_current(msat_ctx *c) {
     return e;
 }
 
-extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float *loss_out,
-                            int64_t *cost_out) {
-    if (!c) return fail(MSAT_EINVAL, "msat_step: ctx is NULL");
-    if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
-    if (flags & ~MSAT_STEP_NO_FINAL_EVAL) return fail(MSAT_EINVAL, "msat_step: unknown flags");
+// Graph of k steps (clause pass and variable pass, k times), captured on a
+// private non-blocking stream: the kernels take the context's device
+// pointers by value, so the graph stays valid for the context's lifetime.
+static cudaError_t capture_steps(msat_ctx *c, int k, cudaGraphExec_t *out) {
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+        cudaError_t le = cudaSuccess;
+        for (int s = 0; s < k && !le; ++s) {
+            le = launch_forward(c->I, c->S, c->D, FWD_STEP, nullptr, cs);
+            if (!le) le = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, cs);
+        }
+        e = cudaStreamEndCapture(cs, &g);
+        if (!e) e = le;
+    }
+    if (!e) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+static constexpr int kGraphSteps = 32;
+
+static cudaError_t graph_steps(msat_ctx *c, int64_t n_steps) {
     cudaError_t e = cudaSuccess;
-    for (int32_t s = 0; s < n_steps && !e; ++s) {
+    if (n_steps >= kGraphSteps && !c->graphK) e = capture_steps(c, kGraphSteps, &c->graphK);
+    if (!e && n_steps % kGraphSteps && !c->graph1) e = capture_steps(c, 1, &c->graph1);
+    for (int64_t s = 0; s + kGraphSteps <= n_steps && !e; s += kGraphSteps)
+        e = cudaGraphLaunch(c->graphK, c->stream);
+    for (int64_t s = 0; s < n_steps % kGraphSteps && !e; ++s) e = cudaGraphLaunch(c->graph1, c->stream);
+    return e;
+}
+
+static cudaError_t plain_steps(msat_ctx *c, int64_t n_steps) {
+    cudaError_t e = cudaSuccess;
+    for (int64_t s = 0; s < n_steps && !e; ++s) {
         prof_begin(c, PROF_FWD);
         e = launch_forward(c->I, c->S, c->D, FWD_STEP, nullptr, c->stream);
         prof_end(c);
@@ -485,6 +524,17 @@ extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float 
         e = launch_backward(c->I, c->S, c->D, BWD_UPDATE, nullptr, nullptr, nullptr, c->stream);
         prof_end(c);
     }
+    return e;
+}
+
+extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float *loss_out,
+                            int64_t *cost_out) {
+    if (!c) return fail(MSAT_EINVAL, "msat_step: ctx is NULL");
+    if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
+    if (flags & ~(MSAT_STEP_NO_FINAL_EVAL | MSAT_STEP_GRAPH))
+        return fail(MSAT_EINVAL, "msat_step: unknown flags");
+    cudaError_t e = ((flags & MSAT_STEP_GRAPH) && !c->prof_on) ? graph_steps(c, n_steps)
+                                                                : plain_steps(c, n_steps);
     if (!e && !(flags & MSAT_STEP_NO_FINAL_EVAL)) e = eval_current(c);
     if (e) return cuda_fail(e, "msat_step: kernel launch");
     c->steps_done_host += n_steps;
@@ -500,6 +550,60 @@ extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float 
 
 extern "C" int msat_step(msat_ctx *c, int32_t n_steps, float *loss_out, int64_t *cost_out) {
     return msat_step_ex(c, n_steps, 0u, loss_out, cost_out);
+}
+
+extern "C" int msat_solve(msat_ctx *c, int64_t max_steps, double time_limit_s, int32_t chunk,
+                          int64_t *steps_out, double *elapsed_out, int64_t *trace_cost,
+                          double *trace_time, int32_t trace_cap, int32_t *trace_len) {
+    if (!c) return fail(MSAT_EINVAL, "msat_solve: ctx is NULL");
+    if (max_steps < 0 || chunk < 1 || trace_cap < 0 || !(time_limit_s >= 0.0))
+        return fail(MSAT_EINVAL, "msat_solve: max_steps >= 0, chunk >= 1, trace_cap >= 0 and "
+                                 "time_limit_s >= 0 required");
+    if (trace_cap > 0 && (!trace_cost || !trace_time))
+        return fail(MSAT_EINVAL, "msat_solve: trace buffers are NULL");
+    const auto t0 = std::chrono::steady_clock::now();
+    auto seconds = [&] {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    std::vector<long long> best((size_t)c->B);
+    int64_t done = 0;
+    int32_t tl = 0;
+    auto read_best = [&](long long *bmin) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(best.data(), c->D.best, sizeof(long long) * best.size(),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        *bmin = *std::min_element(best.begin(), best.end());
+        return e;
+    };
+    auto trace = [&](long long bmin) {
+        if (tl < trace_cap) {
+            trace_cost[tl] = bmin;
+            trace_time[tl] = seconds();
+            ++tl;
+        }
+    };
+    for (;;) {
+        const int64_t k = std::min<int64_t>(chunk, max_steps - done);
+        cudaError_t e = cudaSuccess;
+        if (k > 0) e = c->prof_on ? plain_steps(c, k) : graph_steps(c, k);
+        done += k;
+        long long bmin = 0;
+        if (!e) e = read_best(&bmin);
+        if (e) return cuda_fail(e, "msat_solve");
+        trace(bmin);
+        if (done >= max_steps || bmin == 0 || seconds() >= time_limit_s) break;
+    }
+    // the final x is evaluated once, as msat_step does
+    long long bmin = 0;
+    cudaError_t e = eval_current(c);
+    if (!e) e = read_best(&bmin);
+    if (e) return cuda_fail(e, "msat_solve: final evaluation");
+    trace(bmin);
+    c->steps_done_host += done;
+    if (steps_out) *steps_out = done;
+    if (elapsed_out) *elapsed_out = seconds();
+    if (trace_len) *trace_len = tl;
+    return MSAT_OK;
 }
 
 extern "C" int msat_profile_enable(msat_ctx *c, int on) {

@@ -41,6 +41,9 @@ struct msat_ctx {
     msat::DenseDev dense;
     int8_t *xpm1 = nullptr;       // rounded x as a +-1 batch, allocated on first use
 
+    // CUDA graphs of 1 and kGraphSteps steps (MSAT_STEP_GRAPH), captured on first use
+    cudaGraphExec_t graph1 = nullptr, graphK = nullptr;
+
     // kernel timing (msat_profile_*): event pairs around each launch
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;

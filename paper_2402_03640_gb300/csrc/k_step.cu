@@ -725,7 +725,11 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
             if (imp) D.best[b] = c;
             D.improved[b] = imp;
         }
-        D.cscale[b] = c > 0 ? 2.0f / (float)c : 0.0f;
+        // g_j = (w_j f_j) * 2 / N with N = W_U (mean over the unsat clauses),
+        // 1 (sum over them) or the total weight (mean over all clauses)
+        const int ln = D.sc->loss_norm;
+        const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? D.sc->wsum : c);
+        D.cscale[b] = c > 0 ? 2.0f / den : 0.0f;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -835,7 +839,9 @@ __device__ __forceinline__ void reduce_loss(const DevStep &D, int B, int blk, in
         }
         if (threadIdx.x == 0) {
             const long long c = D.cost[b];
-            D.loss[b] = c > 0 ? s_red[0] / (float)c : 0.0f;
+            const int ln = D.sc->loss_norm;
+            const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? D.sc->wsum : c);
+            D.loss[b] = c > 0 ? s_red[0] / den : 0.0f;
         }
         __syncthreads();
     }

@@ -58,7 +58,7 @@ struct DevInst {
 // Scalars of the optimizer step shared by all restarts.
 struct StepScalars {
     unsigned int counter;   // finished-block counter of the forward kernel
-    unsigned int pad0;
+    int loss_norm;          // MSAT_LOSS_*: normaliser of the loss and of g
     long long steps_done;   // Adam steps taken
     double p1, p2;          // beta1^steps_done, beta2^steps_done (running products)
     float a_t, r_t;         // lr / (1 - p1), 1 / sqrt(1 - p2) of the step in flight

@@ -41,10 +41,16 @@ class msat_config(ctypes.Structure):
                 ("f_mode", ctypes.c_int32), ("seed_x", ctypes.c_uint64),
                 ("heavy_deg", ctypes.c_int32), ("fwd_vw", ctypes.c_int32),
                 ("stage_vw", ctypes.c_int32), ("fwd_blocks", ctypes.c_int32),
-                ("light_rows", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("light_rows", ctypes.c_int32), ("loss_norm", ctypes.c_int32)]
+
+
+class msat_tune_entry(ctypes.Structure):
+    _fields_ = [("fwd_vw", ctypes.c_int32), ("stage_vw", ctypes.c_int32),
+                ("light_rows", ctypes.c_int32), ("ms_per_step", ctypes.c_float)]
 
 
 F_MODES = {"auto": 0, "store": 1, "recompute": 2, "expanded": 3}
+LOSS_NORMS = {"mean_unsat": 0, "sum_unsat": 1, "mean_all": 2}
 
 
 class msat_info(ctypes.Structure):
@@ -89,6 +95,7 @@ class msat_profile(ctypes.Structure):
 
 
 STEP_NO_FINAL_EVAL = 1
+STEP_GRAPH = 2
 PROFILE_KINDS = ("forward", "backward", "evaluate", "other")
 
 _lock = threading.Lock()
@@ -129,6 +136,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_get_state": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "msat_set_state": ([P, P, P, P, P, P, i64, P], ctypes.c_int),
             "msat_step_ex": ([P, i32, ctypes.c_uint32, P, P], ctypes.c_int),
+            "msat_solve": ([P, i64, ctypes.c_double, i32, P, P, P, P, i32, P], ctypes.c_int),
+            "msat_autotune": ([i32, i64, P, P, P, P, P, i32, P, P, i32, P], ctypes.c_int),
             "msat_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
             "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),
             "msat_objective_noalloc": ([i32, i64, P, P, P, P, i32, P, P, P], ctypes.c_int),

@@ -24,6 +24,22 @@ def _p(a) -> Optional[ctypes.c_void_p]:
     return ctypes.c_void_p(a.data_ptr())  # torch tensor
 
 
+def _config(restarts=1, seed_x=1, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, f_mode="auto",
+            heavy_deg=0, fwd_vw=0, stage_vw=0, fwd_blocks=0, light_rows=0, loss_norm="mean_unsat"):
+    lib = native.load()
+    cfg = native.msat_config()
+    check(lib.msat_config_default(ctypes.byref(cfg)))
+    cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
+    cfg.restarts = int(restarts)
+    cfg.seed_x = int(seed_x)
+    cfg.f_mode = native.F_MODES[f_mode]
+    cfg.heavy_deg = int(heavy_deg)
+    cfg.fwd_vw, cfg.stage_vw = int(fwd_vw), int(stage_vw)
+    cfg.fwd_blocks, cfg.light_rows = int(fwd_blocks), int(light_rows)
+    cfg.loss_norm = native.LOSS_NORMS[loss_norm]
+    return cfg
+
+
 def _stream_handle(stream) -> Optional[int]:
     if stream is None:
         try:
@@ -49,18 +65,13 @@ class Solver:
     def __init__(self, n: int, off, lits, weights=None, restarts: int = 1, seed_x: int = 1,
                  lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
                  stream=None, f_mode: str = "auto", heavy_deg: int = 0, fwd_vw: int = 0,
-                 stage_vw: int = 0, fwd_blocks: int = 0, light_rows: int = 0):
+                 stage_vw: int = 0, fwd_blocks: int = 0, light_rows: int = 0,
+                 loss_norm: str = "mean_unsat", tune: bool = False):
         lib = native.load()
         self._lib = lib
-        cfg = native.msat_config()
-        check(lib.msat_config_default(ctypes.byref(cfg)))
-        cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
-        cfg.restarts = int(restarts)
-        cfg.seed_x = int(seed_x)
-        cfg.f_mode = native.F_MODES[f_mode]
-        cfg.heavy_deg = int(heavy_deg)
-        cfg.fwd_vw, cfg.stage_vw = int(fwd_vw), int(stage_vw)
-        cfg.fwd_blocks, cfg.light_rows = int(fwd_blocks), int(light_rows)
+        cfg = _config(restarts=restarts, seed_x=seed_x, lr=lr, beta1=beta1, beta2=beta2, eps=eps,
+                      f_mode=f_mode, heavy_deg=heavy_deg, fwd_vw=fwd_vw, stage_vw=stage_vw,
+                      fwd_blocks=fwd_blocks, light_rows=light_rows, loss_norm=loss_norm)
         off = np.ascontiguousarray(off, dtype=np.int64)
         lits = np.ascontiguousarray(lits, dtype=np.int32)
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)
@@ -69,8 +80,20 @@ class Solver:
         self.B = int(restarts)
         self._ctx = ctypes.c_void_p()
         st = _stream_handle(stream)
+        sp = ctypes.c_void_p(st) if st else None
+        self.tuning = None
+        if tune:  # the launch shape from msat_autotune (results are the same bits)
+            tuned = native.msat_config()
+            ents = (native.msat_tune_entry * 16)()
+            cnt = ctypes.c_int32()
+            check(lib.msat_autotune(self.n, self.m, _p(off), _p(lits), _p(w), ctypes.byref(cfg), sp,
+                                    10, ctypes.byref(tuned), ents, 16, ctypes.byref(cnt)))
+            cfg = tuned
+            self.tuning = {"fwd_vw": cfg.fwd_vw, "stage_vw": cfg.stage_vw, "light_rows": cfg.light_rows,
+                           "timed": [(e.fwd_vw, e.stage_vw, e.light_rows, e.ms_per_step)
+                                     for e in ents[:cnt.value]]}
         check(lib.msat_create(ctypes.byref(self._ctx), self.n, self.m, _p(off), _p(lits), _p(w),
-                              ctypes.byref(cfg), ctypes.c_void_p(st) if st else None))
+                              ctypes.byref(cfg), sp))
 
     @classmethod
     def from_cnf(cls, cnf, **kw) -> "Solver":
@@ -99,18 +122,39 @@ class Solver:
         check(self._lib.msat_set_stream(self._ctx, ctypes.c_void_p(st) if st else None))
 
     # -------------------------------------------------------------- loop
-    def step(self, n_steps: int, want_loss: bool = True, want_cost: bool = True
+    def step(self, n_steps: int, want_loss: bool = True, want_cost: bool = True, graph: bool = False
              ) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
         """n_steps iterations of Algorithm 1 plus a final evaluation; returns
-        (loss at the last updated x, cost of the final x), each [B] or None."""
+        (loss at the last updated x, cost of the final x), each [B] or None.
+        graph: replay the steps from captured CUDA graphs (same bits)."""
         loss = np.empty(self.B, np.float32) if want_loss else None
         cost = np.empty(self.B, np.int64) if want_cost else None
-        check(self._lib.msat_step(self._ctx, int(n_steps), _p(loss), _p(cost)))
+        flags = native.STEP_GRAPH if graph else 0
+        check(self._lib.msat_step_ex(self._ctx, int(n_steps), flags, _p(loss), _p(cost)))
         return loss, cost
 
-    def step_async(self, n_steps: int, final_eval: bool = True) -> None:
-        flags = 0 if final_eval else native.STEP_NO_FINAL_EVAL
+    def step_async(self, n_steps: int, final_eval: bool = True, graph: bool = False) -> None:
+        flags = (0 if final_eval else native.STEP_NO_FINAL_EVAL) | (native.STEP_GRAPH if graph else 0)
         check(self._lib.msat_step_ex(self._ctx, int(n_steps), flags, None, None))
+
+    def solve(self, max_steps: int, time_limit: float = float("inf"), chunk: int = 64,
+              trace_cap: int = 4096) -> dict:
+        """Algorithm 1 with a wall-clock limit (msat_solve): steps in chunks
+        until a restart reaches cost 0, max_steps steps have run or
+        time_limit seconds have passed.  Returns the steps taken, the seconds
+        spent and the (seconds, best cost) trace after each chunk."""
+        steps = ctypes.c_int64()
+        elapsed = ctypes.c_double()
+        tcost = np.empty(trace_cap, np.int64)
+        ttime = np.empty(trace_cap, np.float64)
+        tlen = ctypes.c_int32()
+        limit = min(float(time_limit), 1e300)
+        check(self._lib.msat_solve(self._ctx, int(max_steps), limit, int(chunk), ctypes.byref(steps),
+                                   ctypes.byref(elapsed), _p(tcost), _p(ttime), int(trace_cap),
+                                   ctypes.byref(tlen)))
+        k = tlen.value
+        return {"steps": steps.value, "elapsed_s": elapsed.value,
+                "trace_time_s": ttime[:k].copy(), "trace_best_cost": tcost[:k].copy()}
 
     def profile(self, on: bool = True) -> None:
         """Bracket every kernel of this context with CUDA events."""

@@ -45,7 +45,8 @@ def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, **kw):
 
 
 def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, **kw):
-    ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr)
+    ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr,
+                       loss_norm=kw.get("loss_norm", "mean_unsat"))
     got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk, **kw)
     idx = [0] + [min(k, steps) for k in range(chunk, steps + chunk, chunk)] if steps else [0]
     want_costs = ref["cost_hist"][idx]
@@ -271,3 +272,17 @@ def test_checkpoint_resume_is_bit_identical(pkg, oracle):
     assert np.array_equal(ba[0], bb[0]) and np.array_equal(ba[1], bb[1])
     ref = oracle.solve(cnf, 4, 1, 30, mode=oracle.MODE_F32, lr=1e-2)
     assert np.array_equal(xb.astype(np.float64), ref["x_final"])
+
+
+# ------------------------------------------------ loss normaliser ablation
+
+@pytest.mark.parametrize("loss_norm", ["sum_unsat", "mean_all"])
+@pytest.mark.parametrize("maker", ["ksat", "zipf"])
+def test_loss_normaliser_trajectories(pkg, oracle, loss_norm, maker):
+    """The ablation's other readings of the loss normaliser: the same
+    bit-exact trajectory against the oracle as the default reading."""
+    if maker == "ksat":
+        cnf, B = uniform_ksat(300, 1290, 3, seed=12), 8
+    else:
+        cnf, B = zipf_weighted(900, 3600, seed=13), 4
+    check_bit_exact(oracle, cnf, B, 120, 1e-2, loss_norm=loss_norm)

@@ -289,14 +289,15 @@ def test_invalid_cnf_rejected(oracle):
 
 # ------------------------------------------------------- gradient / loss
 
-@pytest.mark.parametrize("weighted", [False, True])
-def test_gradient_central_differences(oracle, weighted):
+@pytest.mark.parametrize("weighted,loss_norm", [(False, "mean_unsat"), (True, "mean_unsat"),
+                                               (True, "sum_unsat"), (True, "mean_all")])
+def test_gradient_central_differences(oracle, weighted, loss_norm):
     cnf = uniform_ksat(300, 1290, 3, seed=11)
     if weighted:
         cnf = Cnf(n=cnf.n, off=cnf.off, lits=cnf.lits,
                   weights=(1 + np.arange(cnf.m) % 997).astype(np.int64))
     x = oracle.init_x(cnf.n, 2, seed=4).astype(np.float64)
-    base = oracle.objective_f64(cnf, x, want_f=True)
+    base = oracle.objective_f64(cnf, x, want_f=True, loss_norm=loss_norm)
     h = 1e-6
     rng = np.random.default_rng(0)
     idx = [(i, b) for i, b in zip(rng.integers(0, cnf.n, 200), rng.integers(0, 2, 200))
@@ -305,11 +306,39 @@ def test_gradient_central_differences(oracle, weighted):
     for i, b in idx[:60]:
         xp = x.copy(); xp[i, b] += h
         xm = x.copy(); xm[i, b] -= h
-        rp = oracle.objective_f64(cnf, xp, want_f=True, want_grad=False)
-        rm = oracle.objective_f64(cnf, xm, want_f=True, want_grad=False)
+        rp = oracle.objective_f64(cnf, xp, want_f=True, want_grad=False, loss_norm=loss_norm)
+        rm = oracle.objective_f64(cnf, xm, want_f=True, want_grad=False, loss_norm=loss_norm)
         assert np.array_equal(rp["unsat"], base["unsat"]) and np.array_equal(rm["unsat"], base["unsat"])
         fd = (rp["loss"][b] - rm["loss"][b]) / (2 * h)
         assert abs(fd - base["grad"][i, b]) <= 1e-6 * gmax + 1e-10
+
+
+def test_loss_normalisers_closed_form(oracle):
+    """The three readings of the loss normaliser (Sec. 4 "MSE ... over the
+    unsatisfied clauses"): sum_U w f^2 divided by W_U, by 1, by the total
+    weight -- computed here from the oracle's f and unsat mask by numpy."""
+    cnf = zipf_weighted(400, 1600, seed=8)
+    x = oracle.init_x(cnf.n, 3, seed=2).astype(np.float64)
+    w = cnf.weights.astype(np.float64)
+    r = {ln: oracle.objective_f64(cnf, x, want_f=True, loss_norm=ln)
+         for ln in ("mean_unsat", "sum_unsat", "mean_all")}
+    f, u = r["mean_unsat"]["f"], r["mean_unsat"]["unsat"].astype(bool)
+    S = np.array([(w[u[:, b]] * f[u[:, b], b] ** 2).sum() for b in range(3)])
+    WU = np.array([w[u[:, b]].sum() for b in range(3)])
+    assert np.array_equal(WU.astype(np.int64), r["mean_unsat"]["cost"])
+    assert r["mean_unsat"]["loss"] == pytest.approx(S / WU, rel=1e-13)
+    assert r["sum_unsat"]["loss"] == pytest.approx(S, rel=1e-13)
+    assert r["mean_all"]["loss"] == pytest.approx(S / w.sum(), rel=1e-13)
+    # the gradients differ by the same per-restart factors
+    assert r["sum_unsat"]["grad"] == pytest.approx(r["mean_unsat"]["grad"] * WU[None, :], rel=1e-12, abs=1e-14)
+    assert r["mean_all"]["grad"] == pytest.approx(r["sum_unsat"]["grad"] / w.sum(), rel=1e-12, abs=1e-18)
+    for ln in ("sum_unsat", "mean_all"):  # FP32-canon tracks FP64 in every reading
+        b32 = oracle.objective_f32(cnf, x.astype(np.float32), loss_norm=ln)
+        g64 = r[ln]["grad"]
+        assert np.all(np.abs(b32["grad"] - g64) <= 1e-5 * np.abs(g64).max(axis=0)[None, :])
+        assert np.allclose(b32["loss"], r[ln]["loss"], rtol=1e-5, atol=0)
+    # the default is restored after each call
+    assert oracle.objective_f64(cnf, x)["loss"] == pytest.approx(S / WU, rel=1e-13)
 
 
 def test_uniform_weights_reduce_to_unweighted(oracle):
