@@ -309,15 +309,9 @@ def run_ours(args):
     solver.profile(False)
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     dev_ms = float(sum(step_ms))
-    t_max = dev_ms
-    units = float(work_per_step * args.steps)
-    if ws > 1:
-        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([units], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
-        units = float(u.item())
+    from paper_2402_03640_gb300 import replicas
+    t_max, units = replicas.combine(dev_ms, float(work_per_step * args.steps),
+                                    device="cuda" if ws > 1 else None)
     value = units / (t_max / 1e3)
 
     # roofline of the dominant kernel, from the events around each launch
@@ -371,11 +365,9 @@ def run_ours(args):
         s2.step(1)
     t1 = time.perf_counter()
     s2.close()
-    e2e_value = work_per_step * e2e_steps / (t1 - t0)
-    if ws > 1:
-        e = torch.tensor([t1 - t0], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = work_per_step * e2e_steps * ws / float(e.item())
+    e_max, e_units = replicas.combine(t1 - t0, float(work_per_step * e2e_steps),
+                                      device="cuda" if ws > 1 else None)
+    e2e_value = e_units / e_max
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -388,7 +380,7 @@ def run_ours(args):
     info = solver.info()
     serving = None
     if args.workload == DEFAULT_WORKLOAD and args.serve_requests > 0:
-        serving = serve_compare(pkg, args.serve_requests, args.serve_rate)
+        serving = serve_compare(pkg, args.serve_requests, args.serve_rate, rank=rank, world=ws)
     _, cost = solver.step(0, want_loss=False)
     dense_ok = None
     if dense:
@@ -435,13 +427,16 @@ def _pct(xs, q):
     return xs[i]
 
 
-def serve_compare(pkg, count, rate, steps=SERVE_STEPS, B=SERVE_RESTARTS, lr=LR):
+def serve_compare(pkg, count, rate, steps=SERVE_STEPS, B=SERVE_RESTARTS, lr=LR, rank=0, world=1):
     """The first `count` requests of the serving stream, submitted on their
     Poisson arrival schedule (a) to the continuous-batching server and (b) to
     the plain loop that solves one instance at a time (msat_create, msat_step,
     msat_best, msat_destroy).  Latency runs from a request's arrival to its
     result on the host; instances/s = requests / (last result - first arrival)."""
-    reqs = serving_stream(SERVE_STREAM_LEN, rate_per_s=rate, seed=0)[:count]
+    from paper_2402_03640_gb300 import replicas
+    # under N replicas rank r serves every N-th of the first N*count requests
+    reqs = replicas.shard(serving_stream(SERVE_STREAM_LEN, rate_per_s=rate * world, seed=0)[:count * world],
+                          rank, world)
     cnfs = [r.instance() for r in reqs]
     warm = uniform_ksat(300, 1290, 3, seed=123)
 
@@ -485,17 +480,23 @@ def serve_compare(pkg, count, rate, steps=SERVE_STEPS, B=SERVE_RESTARTS, lr=LR):
     h2d = sum(c.off.nbytes + c.lits.nbytes + (0 if c.weights is None else c.weights.nbytes) for c in cnfs)
     d2h = sum(B * 8 + c.n for c in cnfs)
     ks = [r.k for r in reqs]
+    # whole job: all ranks' requests over the slowest rank's makespan
+    _, tot = replicas.combine(0.0, count, device="cuda" if world > 1 else None)
+    span_a, _ = replicas.combine(span_a, 0.0, device="cuda" if world > 1 else None)
+    span_b, _ = replicas.combine(span_b, 0.0, device="cuda" if world > 1 else None)
+    count_all = int(tot)
     return {
-        "instances_per_s": count / span_a,
+        "instances_per_s": count_all / span_a,
         "p50_ms": 1e3 * _pct(lat_a, 50), "p99_ms": 1e3 * _pct(lat_a, 99),
-        "one_at_a_time": {"instances_per_s": count / span_b, "p50_ms": 1e3 * _pct(lat_b, 50),
+        "one_at_a_time": {"instances_per_s": count_all / span_b, "p50_ms": 1e3 * _pct(lat_b, 50),
                           "p99_ms": 1e3 * _pct(lat_b, 99)},
         "speedup_vs_one_at_a_time": span_b / span_a,
         "final_costs_equal": bool(equal),
         "mean_best_cost": float(np.mean([x["best_cost"] for x in served])),
-        "served_literal_evals_per_s": lit_evals / span_a,
+        "served_literal_evals_per_s": lit_evals * world / span_a,
         "peak_running": st["peak_running"], "graph_captures": st["graph_captures"],
-        "requests": count, "arrival_rate_per_s": rate, "steps": steps, "restarts": B, "lr": lr,
+        "requests": count_all, "requests_per_rank": count, "arrival_rate_per_s": rate * world,
+        "steps": steps, "restarts": B, "lr": lr,
         "k_counts": {str(k): ks.count(k) for k in (3, 4, 5)},
         "n_range": [min(r.n for r in reqs), max(r.n for r in reqs)],
         "h2d_bytes_per_request": h2d / count, "d2h_bytes_per_request": d2h / count,
@@ -523,14 +524,9 @@ def run_serving(args):
     clocks.start()
     if ws > 1:
         torch.distributed.barrier()
-    res = serve_compare(pkg, args.serve_requests, args.serve_rate)
+    res = serve_compare(pkg, args.serve_requests, args.serve_rate, rank=rank, world=ws)
     clk = clocks.stop()
     value = res["instances_per_s"]
-    if ws > 1:
-        # every rank serves its own copy of the stream: instances/s add up
-        t = torch.tensor([value], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        value = float(t.item())
     line = {
         "metric": "instances/s", "value": value, "unit": "instances/s", "n_gpus": ws,
         "steps": res["steps"], "warmup": 1, "ms_per_step": None, "higher_is_better": True,
