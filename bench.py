@@ -339,7 +339,7 @@ def run_ours(args):
         with open(tfile) as f:
             tr = json.load(f)
         ent = tr.get(args.workload, {}).get(dom)
-        if ent and ent.get("kernel_hash") == kernel_hash():
+        if ent and ent.get("kernel_hash") == kernel_hash(dom):
             traffic = ent["bytes_per_launch"]
     if per_kernel[dom]["bound"] == "tensor":
         ach = per_kernel[dom]["tflops"]
@@ -548,12 +548,17 @@ def run_serving(args):
     return 0
 
 
-def kernel_hash():
-    """Hash of the step-kernel sources, to tell whether stored ncu traffic is stale."""
+KERNEL_SOURCES = {"forward": ("k_step.cu", "msat_internal.cuh"),
+                  "backward": ("k_step.cu", "msat_internal.cuh"),
+                  "dense_eval": ("k_dense.cu", "msat_internal.cuh")}
+
+
+def kernel_hash(kind="forward"):
+    """Hash of a kernel's sources, to tell whether stored ncu traffic is stale."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_03640_gb300", "csrc")
-    for name in ("k_step.cu", "msat_internal.cuh"):
+    for name in KERNEL_SOURCES[kind]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
