@@ -22,6 +22,10 @@ Instance families (all clause lists use DIMACS literals: +(i+1) for x_i,
                       elements (optimum cost 1).
 * serving_stream   -- a stream of random k-SAT requests with Poisson
                       arrivals for the serving loop.
+* partial_maxsat   -- hard and soft clauses as one weighted instance: each
+                      hard clause weighs 1 + the total soft weight.
+* random_partial   -- planted k-SAT hard clauses plus weighted soft unit
+                      clauses.
 
 The two structured families follow the principles' mathematical definitions;
 their variable and clause counts agree with the paper's Table 2 (PHP and GT
@@ -315,3 +319,30 @@ def serving_stream(count: int, rate_per_s: float, seed: int = 0, n_lo: int = 100
     arrivals = np.cumsum(gaps)
     return [Request(rid=i, arrival_s=float(arrivals[i]), k=int(ks[i]), n=int(ns[i]), m=int(ms[i]),
                     seed=int(_substream(seed, 1000 + i) & 0x7FFFFFFF)) for i in range(count)]
+
+
+def partial_maxsat(n: int, hard, soft, soft_weights) -> Cnf:
+    """Partial MaxSAT (hard clauses must hold, soft ones carry weights) as
+    one weighted instance: every hard clause weighs top = 1 + sum of the soft
+    weights, so violating any hard clause costs more than violating all soft
+    ones.  An assignment of cost < top satisfies every hard clause, and its
+    cost is then its soft cost."""
+    soft_weights = [int(w) for w in soft_weights]
+    if len(soft_weights) != len(soft) or any(w < 1 for w in soft_weights):
+        raise ValueError("one weight >= 1 per soft clause")
+    top = 1 + sum(soft_weights)
+    return Cnf.from_clauses(n, list(hard) + list(soft), weights=[top] * len(hard) + soft_weights,
+                            name=f"partial_n{n}_h{len(hard)}_s{len(soft)}")
+
+
+def random_partial(n: int, m_hard: int, m_soft: int, k: int = 3, seed: int = 0) -> Cnf:
+    """Hard clauses: planted k-SAT (satisfiable); soft clauses: unit clauses
+    on distinct-by-draw variables with random signs, weights uniform 1..9."""
+    hard = planted_ksat(n, m_hard, k, seed=seed).clauses()
+    s = _substream(seed, 31)
+    idx = np.arange(m_soft, dtype=np.uint64)
+    var = _below(splitmix64(s, 3 * idx), n)
+    sign = (splitmix64(s, 3 * idx + np.uint64(1)) & np.uint64(1)).astype(bool)
+    w = 1 + _below(splitmix64(s, 3 * idx + np.uint64(2)), 9)
+    soft = [[int(v) + 1 if sg else -(int(v) + 1)] for v, sg in zip(var, sign)]
+    return partial_maxsat(n, hard, soft, [int(x) for x in w])
