@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import serving_stream, uniform_ksat, zipf_weighted  # noqa: E402
+from synth import ordering, pigeonhole, serving_stream, uniform_ksat, zipf_weighted  # noqa: E402
 
 L2_BYTES = 129 * 2 ** 20
 
@@ -54,6 +54,9 @@ SERVING = "serving_k345_b8"
 SERVE_STREAM_LEN = 10000
 SERVE_STEPS = 1000
 SERVE_RESTARTS = 8
+# cost-vs-time curves of Algorithm 1 with its time limit on the structured
+# families of Table 2 (pigeonhole PHP and ordering GT, optimum cost 1)
+STRUCTURED = "structured_cost_time"
 # workloads whose step also runs the dense tensor-core evaluation of the rounded batch
 DENSE_EVAL = {"ksat3_n5000_m21500_b256"}
 LR = 1e-4
@@ -203,6 +206,10 @@ def run_reference(args):
         return 0
     if args.workload == SERVING:
         return run_reference_serving(args)
+    if args.workload == STRUCTURED:
+        print(json.dumps({"impl": "reference", "unavailable": "the cost-vs-time curves have no oracle arm: "
+                          "the oracle has no wall-clock limit"}), flush=True)
+        return 0
     gen, B, desc = WORKLOADS[args.workload]
     cnf = gen()
     from oracle import oracle
@@ -506,6 +513,43 @@ def serve_compare(pkg, count, rate, steps=SERVE_STEPS, B=SERVE_RESTARTS, lr=LR, 
     }
 
 
+def run_structured(args):
+    import torch
+    import paper_2402_03640_gb300 as pkg
+    from paper_2402_03640_gb300 import build as pkg_build
+
+    ws, rank, _ = dist_env()
+    torch.cuda.set_device(0 if ws == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    pkg_build.build()
+    pkg.load()
+    fams = [("php", h, pigeonhole(h)) for h in (10, 20, 30, 40, 50)] + \
+           [("gt", s, ordering(s)) for s in (10, 20, 30)]
+    curves, at_opt = {}, 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for fam, size, cnf in fams:
+        with pkg.Solver.from_cnf(cnf, restarts=8, lr=LR) as s:
+            r = s.solve(10 ** 12, time_limit=args.time_limit, chunk=256)
+        t, c = r["trace_time_s"], r["trace_best_cost"]
+        keep = [0] + [i for i in range(1, len(c)) if c[i] < c[i - 1]] + [len(c) - 1]
+        best = int(c[-1])
+        at_opt += best == 1
+        curves[f"{fam}{size}"] = {"n": cnf.n, "m": cnf.m, "steps": r["steps"], "seconds": r["elapsed_s"],
+                                  "best_cost": best,
+                                  "trace": [[round(float(t[i]), 4), int(c[i])] for i in sorted(set(keep))]}
+    clk = clocks.stop()
+    line = {"metric": "structured families at the optimum (cost 1) within the time limit",
+            "value": at_opt, "unit": "instances", "n_gpus": 1, "steps": None, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": STRUCTURED, "time_limit_s": args.time_limit, "restarts": 8, "lr": LR,
+                       "families": "pigeonhole PHP(h) h in {10..50}, ordering GT(s) s in {10, 20, 30}"},
+            "curves": curves, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     import torch
     import paper_2402_03640_gb300 as pkg
@@ -570,7 +614,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SERVING], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SERVING, STRUCTURED],
+                    default=DEFAULT_WORKLOAD)
+    ap.add_argument("--time-limit", type=float, default=1.0,
+                    help="seconds per instance of the structured cost-vs-time workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving comparison (0: skip it on the default line)")
@@ -582,6 +629,8 @@ def main():
         return run_reference(args)
     if args.workload == SERVING:
         return run_serving(args)
+    if args.workload == STRUCTURED:
+        return run_structured(args)
     return run_ours(args)
 
 

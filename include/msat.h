@@ -245,6 +245,19 @@ int msat_evaluate_x(msat_ctx *ctx, int32_t backend, int64_t *cost_out);
 int msat_check(msat_ctx *ctx);
 
 /*
+ * The paper's quick evaluation reads clause j as satisfied when f_j > 0
+ * (Sec. 4, "Example": a positive clause value marks a satisfied clause);
+ * the exact test is "some literal is true under x > 0" (Sec. 4,
+ * "Unsatisfiable Cores").  For the current x this counts, per restart,
+ * the clauses the quick reading calls unsatisfied (f_j <= 0) and the
+ * clauses on which the two readings disagree, with f_j in the step's fixed
+ * summation order.  Diagnostic for the readings ablation.
+ *   heur_unsat, disagree   host int64[B]
+ * Synchronous; EINVAL on NULL arguments, ECUDA on a CUDA failure.
+ */
+int msat_heuristic_gap(msat_ctx *ctx, int64_t *heur_unsat, int64_t *disagree);
+
+/*
  * Best assignment and cost seen so far per restart (Alg. 1 lines 5-7).
  *   assign01   host uint8[B][n] (0/1), or NULL
  *   best_cost  host int64[B], or NULL

@@ -746,6 +746,22 @@ extern "C" int msat_evaluate_x(msat_ctx *c, int32_t backend, int64_t *cost_out) 
     return msat_evaluate(c, c->xpm1, c->B, cost_out, backend);
 }
 
+extern "C" int msat_heuristic_gap(msat_ctx *c, int64_t *heur_unsat, int64_t *disagree) {
+    if (!c || !heur_unsat || !disagree) return fail(MSAT_EINVAL, "msat_heuristic_gap: NULL argument");
+    if (!c->hgap) {
+        const int rc = dalloc_t(c, &c->hgap, (size_t)2 * c->B);  // freed with the context
+        if (rc) return rc;
+    }
+    long long *d = c->hgap;
+    cudaError_t e = launch_heuristic_gap(c->I, c->S.x, d, d + c->B, c->stream);
+    if (!e) e = cudaMemcpyAsync(heur_unsat, d, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(disagree, d + c->B, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost,
+                                c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(e, "msat_heuristic_gap");
+    return MSAT_OK;
+}
+
 extern "C" int msat_best(msat_ctx *c, uint8_t *assign01, int64_t *best_cost) {
     if (!c) return fail(MSAT_EINVAL, "msat_best: ctx is NULL");
     if (best_cost)

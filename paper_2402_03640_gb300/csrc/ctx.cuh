@@ -40,6 +40,7 @@ struct msat_ctx {
     bool dense_ready = false;
     msat::DenseDev dense;
     int8_t *xpm1 = nullptr;       // rounded x as a +-1 batch, allocated on first use
+    long long *hgap = nullptr;    // [2][B] counts of msat_heuristic_gap, allocated on first use
 
     // CUDA graphs of 1 and kGraphSteps steps (MSAT_STEP_GRAPH), captured on first use
     cudaGraphExec_t graph1 = nullptr, graphK = nullptr;

@@ -35,6 +35,7 @@ namespace {
 constexpr int kTM = 128;            // clauses per tile (MMA M)
 constexpr int kTK = 128;            // variables per stage (128 bytes of e4m3)
 constexpr int kStages = 4;
+constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
 constexpr long long kSpin = 1LL << 26;
@@ -89,6 +90,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+// L2 prefetch of one tile of a tensor map (no shared memory, no barrier):
+// the clause-matrix tiles are streamed from HBM once, so fetching them into
+// L2 ahead of their TMA loads turns each load's latency into an L2 hit.
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -183,10 +194,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     const uint32_t tmem = H->tmem;
 
     if (warp == 0 && lane == 0) {
-        // producer: TMA loads of the A (clause rows) and B (assignment rows) tiles
+        // producer: TMA loads of the A (clause rows) and B (assignment rows)
+        // tiles; the A tiles are prefetched into L2 kPrefetch k-tiles ahead
+        // (x = kt * 128 bytes: 16-byte aligned)
+        for (int kt = 0; kt < kt_count && kt < kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kTK, m0);
         int issued = 0;
         for (int kt = 0; kt < kt_count; ++kt) {
             const int s = kt % kStages;
+            if (kt + kPrefetch < kt_count) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kTK, m0);
             if (kt >= kStages) {
                 const uint32_t parity = (uint32_t)((kt / kStages - 1) & 1);
                 if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, kSpin)) {

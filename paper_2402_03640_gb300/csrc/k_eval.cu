@@ -80,6 +80,68 @@ __global__ void k_round_pm1(const float *__restrict__ x, int8_t *__restrict__ a,
         a[q] = __ldg(x + q) > 0.0f ? (int8_t)1 : (int8_t)-1;
 }
 
+// The paper's quick reading of a clause as satisfied when f_j > 0 (Sec. 4,
+// "Example") against the exact test (some literal true under x > 0).  One
+// thread per (clause, restart): f_j in the fixed order of the step (terms in
+// literal order, 32-term leaves, dyadic combination) from t = tanh(x);
+// counts per restart the clauses read as unsat by the heuristic and those on
+// which the two tests disagree.  Integer counts, so the order of the
+// additions does not matter.
+__global__ void k_heuristic_gap(DevInst I, const float *__restrict__ x,
+                                unsigned long long *__restrict__ heur_unsat,
+                                unsigned long long *__restrict__ disagree) {
+    const int B = I.B;
+    const long long total = (long long)I.m * B;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / B), b = (int)(q - (long long)j * B);
+        int beg, end;
+        if (I.kfix > 0) {
+            beg = j * I.kfix;
+            end = beg + I.kfix;
+        } else {
+            beg = __ldg(I.coff + j);
+            end = __ldg(I.coff + j + 1);
+        }
+        LeafCounter<6> lc;
+        lc.init();
+        float leaf = 0.0f;
+        int in_leaf = 0;
+        bool sat = false;
+        for (int p = beg; p < end; ++p) {
+            const int L = __ldg(I.lit + p);
+            const float xv = __ldg(x + (long long)(L >> 1) * B + b);
+            const float tv = tanh_fixed(xv);
+            const bool neg = L & 1;
+            const float term = neg ? -tv : tv;
+            leaf = in_leaf == 0 ? term : leaf + term;
+            sat |= (xv > 0.0f) != neg;
+            if (++in_leaf == 32) {
+                lc.push(leaf);
+                in_leaf = 0;
+            }
+        }
+        if (in_leaf) lc.push(leaf);
+        const float f = lc.finish();
+        if (!(f > 0.0f)) atomicAdd(heur_unsat + b, 1ull);
+        if ((f > 0.0f) != sat) atomicAdd(disagree + b, 1ull);
+    }
+}
+
+cudaError_t launch_heuristic_gap(const DevInst &I, const float *x, long long *heur_unsat,
+                                 long long *disagree, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(heur_unsat, 0, sizeof(long long) * (size_t)I.B, st);
+    if (!e) e = cudaMemsetAsync(disagree, 0, sizeof(long long) * (size_t)I.B, st);
+    if (e) return e;
+    const long long total = (long long)I.m * I.B;
+    long long blocks = (total + kThreads - 1) / kThreads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_heuristic_gap<<<(unsigned)blocks, kThreads, 0, st>>>(I, x, reinterpret_cast<unsigned long long *>(heur_unsat),
+                                                           reinterpret_cast<unsigned long long *>(disagree));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_round_pm1(const float *x, int8_t *a, long long count, cudaStream_t st) {
     long long blocks = (count + kThreads - 1) / kThreads;
     if (blocks > 152 * 16) blocks = 152 * 16;

@@ -247,6 +247,8 @@ cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
                                cudaStream_t st);
 cudaError_t launch_round_pm1(const float *x, int8_t *a, long long count, cudaStream_t st);
+cudaError_t launch_heuristic_gap(const DevInst &I, const float *x, long long *heur_unsat,
+                                 long long *disagree, cudaStream_t st);
 int dense_tile_n(int nb);
 int dense_rows(int nb);
 size_t dense_smem_bytes(int ntile);

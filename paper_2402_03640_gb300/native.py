@@ -138,6 +138,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_step_ex": ([P, i32, ctypes.c_uint32, P, P], ctypes.c_int),
             "msat_solve": ([P, i64, ctypes.c_double, i32, P, P, P, P, i32, P], ctypes.c_int),
             "msat_autotune": ([i32, i64, P, P, P, P, P, i32, P, P, i32, P], ctypes.c_int),
+            "msat_heuristic_gap": ([P, P, P], ctypes.c_int),
             "msat_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
             "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),
             "msat_objective_noalloc": ([i32, i64, P, P, P, P, i32, P, P, P], ctypes.c_int),

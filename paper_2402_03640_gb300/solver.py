@@ -218,6 +218,14 @@ class Solver:
         check(self._lib.msat_evaluate(self._ctx, _p(a), nb, _p(out), be))
         return out
 
+    def heuristic_gap(self) -> Tuple[np.ndarray, np.ndarray]:
+        """(clauses the quick f_j > 0 reading calls unsat, clauses on which it
+        disagrees with the exact test), each int64 [B], at the current x."""
+        hu = np.empty(self.B, np.int64)
+        dg = np.empty(self.B, np.int64)
+        check(self._lib.msat_heuristic_gap(self._ctx, _p(hu), _p(dg)))
+        return hu, dg
+
     def evaluate_x(self, backend: str = "sparse", out=None):
         """Exact cost of the current x rounded to +-1, as a torch int64 CUDA
         tensor [B] (written into out when given)."""

@@ -286,3 +286,20 @@ def test_loss_normaliser_trajectories(pkg, oracle, loss_norm, maker):
     else:
         cnf, B = zipf_weighted(900, 3600, seed=13), 4
     check_bit_exact(oracle, cnf, B, 120, 1e-2, loss_norm=loss_norm)
+
+
+@pytest.mark.parametrize("maker", ["ksat", "php"])
+def test_heuristic_gap_matches_oracle(pkg, oracle, maker):
+    """The quick f_j > 0 reading of Sec. 4 against the exact test: counts
+    of heuristic-unsat clauses and of disagreements per restart equal those
+    derived from the oracle's FP32-canon f and unsat mask at the same x
+    (PHP(40) has 40-literal clauses: several summation leaves)."""
+    cnf = uniform_ksat(400, 1720, 3, seed=14) if maker == "ksat" else pigeonhole(40)
+    with pkg.Solver.from_cnf(cnf, restarts=4, lr=1e-2) as s:
+        s.step(30)
+        x = s.x()
+        hu, dg = s.heuristic_gap()
+    r = oracle.objective_f32(cnf, x, want_f=True, want_grad=False)
+    f, sat = r["f"], r["unsat"] == 0
+    assert np.array_equal(hu, (~(f > 0)).sum(axis=0))
+    assert np.array_equal(dg, ((f > 0) != sat).sum(axis=0))
