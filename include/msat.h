@@ -159,9 +159,15 @@ int msat_step(msat_ctx *ctx, int32_t n_steps, float *loss_out, int64_t *cost_out
  * stream); the results are bit for bit those of the plain launches.  It is
  * ignored while kernel timing (msat_profile_enable) is on.  A graph holds
  * the context's device pointers; it is released with the context.
+ * Small instances (B <= 64, 4 n B + m B floats within 200 KiB of shared
+ * memory, no variable with more than 32736 occurrences) run all their steps
+ * in one single-CTA launch holding the state in shared memory, again with
+ * the same bits; MSAT_STEP_PER_PASS keeps them on the per-pass kernels (for
+ * comparison), as does kernel timing.
  */
 #define MSAT_STEP_NO_FINAL_EVAL 1u
 #define MSAT_STEP_GRAPH 2u
+#define MSAT_STEP_PER_PASS 4u
 int msat_step_ex(msat_ctx *ctx, int32_t n_steps, uint32_t flags, float *loss_out,
                  int64_t *cost_out);
 
@@ -296,6 +302,8 @@ typedef struct {
     int32_t max_degree;   /* most occurrences of one variable                  */
     int32_t n_heavy;      /* variables whose occurrence sum is split across warps */
     int32_t uniform_len;  /* common clause length, or 0 if lengths differ      */
+    int32_t small_kernel; /* 1: msat_step runs the single-CTA kernel (all steps
+                             of a call in one launch, state in shared memory) */
 } msat_info;
 
 int msat_get_info(msat_ctx *ctx, msat_info *info);

@@ -527,14 +527,27 @@ static cudaError_t plain_steps(msat_ctx *c, int64_t n_steps) {
     return e;
 }
 
+// k steps by the fastest route that gives the same bits: the single-CTA
+// kernel for small instances, captured graphs when asked, else plain
+// launches (always plain while kernel timing is on, so every pass is timed).
+static cudaError_t run_steps(msat_ctx *c, int64_t k, uint32_t flags) {
+    if (c->prof_on) return plain_steps(c, k);
+    if (!(flags & MSAT_STEP_PER_PASS) && small_fits(c->I, c->max_deg)) {
+        cudaError_t e = cudaSuccess;
+        for (int64_t done = 0; done < k && !e; done += (1 << 30))
+            e = launch_small_steps(c->I, c->S, c->D, (int)std::min<int64_t>(k - done, 1 << 30), c->stream);
+        return e;
+    }
+    return (flags & MSAT_STEP_GRAPH) ? graph_steps(c, k) : plain_steps(c, k);
+}
+
 extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float *loss_out,
                             int64_t *cost_out) {
     if (!c) return fail(MSAT_EINVAL, "msat_step: ctx is NULL");
     if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
-    if (flags & ~(MSAT_STEP_NO_FINAL_EVAL | MSAT_STEP_GRAPH))
+    if (flags & ~(MSAT_STEP_NO_FINAL_EVAL | MSAT_STEP_GRAPH | MSAT_STEP_PER_PASS))
         return fail(MSAT_EINVAL, "msat_step: unknown flags");
-    cudaError_t e = ((flags & MSAT_STEP_GRAPH) && !c->prof_on) ? graph_steps(c, n_steps)
-                                                                : plain_steps(c, n_steps);
+    cudaError_t e = run_steps(c, n_steps, flags);
     if (!e && !(flags & MSAT_STEP_NO_FINAL_EVAL)) e = eval_current(c);
     if (e) return cuda_fail(e, "msat_step: kernel launch");
     c->steps_done_host += n_steps;
@@ -585,7 +598,7 @@ extern "C" int msat_solve(msat_ctx *c, int64_t max_steps, double time_limit_s, i
     for (;;) {
         const int64_t k = std::min<int64_t>(chunk, max_steps - done);
         cudaError_t e = cudaSuccess;
-        if (k > 0) e = c->prof_on ? plain_steps(c, k) : graph_steps(c, k);
+        if (k > 0) e = run_steps(c, k, MSAT_STEP_GRAPH);
         done += k;
         long long bmin = 0;
         if (!e) e = read_best(&bmin);
@@ -805,6 +818,7 @@ extern "C" int msat_get_info(msat_ctx *c, msat_info *info) {
     info->max_degree = c->max_deg;
     info->n_heavy = c->I.n_heavy;
     info->uniform_len = c->kfix;
+    info->small_kernel = small_fits(c->I, c->max_deg) ? 1 : 0;
     return MSAT_OK;
 }
 

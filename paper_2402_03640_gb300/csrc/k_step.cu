@@ -1282,4 +1282,215 @@ cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------- small instances
+// k_small_steps: n_steps iterations of Algorithm 1 for a small instance in
+// one launch of one CTA, with x, the Adam moments, t = tanh(x) and the
+// clause pass's w*f (NaN where satisfied) held in shared memory; literal
+// and occurrence lists are read through L1.  Per step: the clause pass
+// (one thread per (clause, restart), the fixed literal order with 32-term
+// leaves), the per-restart scalars (cost, best, 2/N, the Adam products in
+// double), the variable pass (one thread per (variable, restart), the
+// fixed occurrence order with 32-term leaves and the dyadic counter, then
+// the same Adam update and tanh), each separated by a block barrier.  Every
+// value that enters x is computed with the operations of the per-pass
+// kernels, so the trajectory is the same bit for bit; the state left in
+// device memory (x, moments, t in the buffer of the step parity, best,
+// cost, scalars) is what those kernels leave.  The loss partials are summed
+// in another order (the loss is reported, never fed back).
+
+__device__ __forceinline__ float small_clause_f(const DevInst &I, const float *__restrict__ st,
+                                                int j, int b, bool &sat) {
+    const int B = I.B;
+    int beg, end;
+    clause_range(I, I.kfix, j, beg, end);
+    LeafCounter<6> lc;
+    lc.init();
+    float leaf = 0.0f;
+    int in_leaf = 0;
+    sat = false;
+    for (int p = beg; p < end; ++p) {
+        const int L = __ldg(I.lit + p);
+        const bool neg = L & 1;
+        const float tv = st[(L >> 1) * B + b];
+        const float term = neg ? -tv : tv;
+        leaf = in_leaf == 0 ? term : leaf + term;
+        sat |= (tv > 0.0f) != neg;
+        if (++in_leaf == 32) {
+            lc.push(leaf);
+            in_leaf = 0;
+        }
+    }
+    if (lc.cnt == 0) return in_leaf ? leaf : 0.0f;  // at most 32 literals: the leaf itself
+    if (in_leaf) lc.push(leaf);
+    return lc.finish();
+}
+
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    k_small_steps(DevInst I, DevState S, DevStep D, int n_steps) {
+    extern __shared__ float4 small_smem[];
+    __shared__ unsigned long long s_wu[kSmallMaxB];
+    __shared__ float s_lsum[kSmallMaxB];
+    __shared__ float s_lp[kSmallThreads];
+    __shared__ long long s_cost[kSmallMaxB], s_best[kSmallMaxB];
+    __shared__ int s_imp[kSmallMaxB];
+    __shared__ float s_cs[kSmallMaxB];
+    __shared__ float s_at, s_rt;
+    const int B = I.B;
+    const int nB = I.n * B, mB = I.m * B;
+    float *sx = reinterpret_cast<float *>(small_smem);
+    float *smo = sx + nB, *sve = smo + nB, *st = sve + nB, *sq = st + nB;
+    StepScalars *sc = D.sc;
+    const long long steps0 = sc->steps_done;
+    const float *t_in = (steps0 & 1) ? S.t1 : S.t0;
+    for (int q = threadIdx.x; q < nB; q += blockDim.x) {
+        sx[q] = S.x[q];
+        smo[q] = S.mom[q];
+        sve[q] = S.vel[q];
+        st[q] = t_in[q];
+    }
+    for (int b = threadIdx.x; b < B; b += blockDim.x) s_best[b] = D.best[b];
+    const AdamView A0 = adam_view(sc);
+    const int ln = sc->loss_norm;
+    const long long wsum = sc->wsum;
+    double p1 = sc->p1, p2 = sc->p2;  // used by thread 0
+    __syncthreads();
+    for (int step = 0; step < n_steps; ++step) {
+        for (int b = threadIdx.x; b < B; b += blockDim.x) s_wu[b] = 0ull;
+        __syncthreads();
+        // clause pass: f, exact unsat test, w*f (NaN where satisfied), sums.
+        // The item stride (the block) is a multiple of B, so a thread keeps
+        // one restart and its loss partial is one float.
+        float lpart = 0.0f;
+        for (int it = threadIdx.x; it < mB; it += blockDim.x) {
+            const int j = it / B, b = it - j * B;
+            bool sat;
+            const float f = small_clause_f(I, st, j, b, sat);
+            float q = __int_as_float(0x7fc00000);
+            if (!sat) {
+                const long long wj = I.w ? __ldg(I.w + j) : 1ll;
+                q = (float)wj * f;
+                atomicAdd(&s_wu[b], (unsigned long long)wj);
+                lpart += q * f;
+            }
+            sq[it] = q;
+        }
+        // loss partials in a fixed order: lanes of a restart by a shuffle
+        // tree, then the warp partials in warp order
+        for (int o = B; o < 32; o <<= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
+        s_lp[threadIdx.x] = lpart;
+        __syncthreads();
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            const int stride = B < 32 ? 32 : B;
+            float sum = 0.0f;
+            for (int k = b; k < kSmallThreads; k += stride) sum += s_lp[k];
+            s_lsum[b] = sum;
+        }
+        // per-restart scalars, as the clause pass's last block computes them
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            const long long c = (long long)s_wu[b];
+            const int imp = c < s_best[b];
+            if (imp) s_best[b] = c;
+            s_cost[b] = c;
+            s_imp[b] = imp;
+            const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? wsum : c);
+            s_cs[b] = c > 0 ? 2.0f / den : 0.0f;
+        }
+        if (threadIdx.x == 0) {
+            p1 = p1 * sc->beta1;
+            p2 = p2 * sc->beta2;
+            s_at = (float)(sc->lr / (1.0 - p1));
+            s_rt = (float)(1.0 / sqrt(1.0 - p2));
+        }
+        __syncthreads();
+        AdamView A = A0;
+        A.a_t = s_at;
+        A.r_t = s_rt;
+        // variable pass: occurrence sum, gradient, best capture, Adam, tanh
+        for (int it = threadIdx.x; it < nB; it += blockDim.x) {
+            const int i = it / B, b = it - i * B;
+            const int vb = __ldg(I.voff + i), ve = __ldg(I.voff + i + 1);
+            const float cs = s_cs[b];
+            LeafCounter<10> lc;
+            lc.init();
+            float leaf = 0.0f;
+            int in_leaf = 0;
+            for (int p = vb; p < ve; ++p) {
+                const int o = __ldg(I.occ + p);
+                const float qv = sq[(o >> I.occ_shift) * B + b];
+                const float g = qv * cs;
+                const float term = (qv != qv) ? 0.0f : ((o & 1) ? -g : g);
+                leaf = in_leaf == 0 ? term : leaf + term;
+                if (++in_leaf == 32) {
+                    lc.push(leaf);
+                    in_leaf = 0;
+                }
+            }
+            if (in_leaf) lc.push(leaf);
+            const float Ssum = lc.finish();
+            const float tv = st[it];
+            const float gr = Ssum * fmaf(-tv, tv, 1.0f);
+            float xv = sx[it], mv = smo[it], vv = sve[it];
+            if (s_imp[b]) S.bestx[it] = xv > 0.0f;
+            if (s_cost[b] != 0) {
+                xv = adam_update(A, xv, mv, vv, gr);
+                sx[it] = xv;
+                smo[it] = mv;
+                sve[it] = vv;
+                st[it] = tanh_fixed(xv);
+            }
+        }
+        __syncthreads();
+    }
+    // the state the per-pass kernels leave
+    float *t_out = ((steps0 + n_steps) & 1) ? S.t1 : S.t0;
+    for (int q = threadIdx.x; q < nB; q += blockDim.x) {
+        S.x[q] = sx[q];
+        S.mom[q] = smo[q];
+        S.vel[q] = sve[q];
+        t_out[q] = st[q];
+    }
+    if (S.fstore)
+        for (int q = threadIdx.x; q < mB; q += blockDim.x) S.fstore[q] = sq[q];
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        D.cost[b] = s_cost[b];
+        D.best[b] = s_best[b];
+        D.improved[b] = s_imp[b];
+        D.cscale[b] = s_cs[b];
+        const long long c = s_cost[b];
+        const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? wsum : c);
+        D.loss[b] = c > 0 ? s_lsum[b] / den : 0.0f;
+    }
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int b = 0; b < B; ++b) tot += s_cost[b];
+        sc->dense = (double)tot * 16.0 > (double)wsum * (double)B;
+        sc->p1 = p1;
+        sc->p2 = p2;
+        sc->a_t = s_at;
+        sc->r_t = s_rt;
+        sc->steps_done = steps0 + n_steps;
+    }
+}
+
+size_t small_smem_bytes(const DevInst &I) {
+    return sizeof(float) * (4 * (size_t)I.n * I.B + (size_t)I.m * I.B);
+}
+
+bool small_fits(const DevInst &I, int max_deg) {
+    return I.B <= kSmallMaxB && small_smem_bytes(I) <= kSmallSmemMax && max_deg <= 32 * 1023 &&
+           (long long)I.m * I.B <= (1LL << 30);
+}
+
+cudaError_t launch_small_steps(const DevInst &I, const DevState &S, const DevStep &D, int n_steps,
+                               cudaStream_t st) {
+    if (n_steps <= 0) return cudaSuccess;
+    const size_t smem = small_smem_bytes(I);
+    cudaError_t e = cudaFuncSetAttribute(k_small_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmallSmemMax);
+    if (e) return e;
+    k_small_steps<<<1, kSmallThreads, smem, st>>>(I, S, D, n_steps);
+    return cudaGetLastError();
+}
+
 }  // namespace msat

@@ -244,6 +244,15 @@ cudaError_t launch_step_batch(const SlotDesc *slots, int nslot, const int *fwd_s
 int heavy_blocks_of(const DevInst &I);
 int light_blocks_of(const DevInst &I);
 cudaError_t launch_loss_reduce(const DevStep &D, int B, cudaStream_t st);
+// Small instances: every step in one single-CTA launch with the state in
+// shared memory (same bits as the per-pass kernels).
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxB = 64;
+constexpr size_t kSmallSmemMax = 200 * 1024;
+size_t small_smem_bytes(const DevInst &I);
+bool small_fits(const DevInst &I, int max_deg);
+cudaError_t launch_small_steps(const DevInst &I, const DevState &S, const DevStep &D, int n_steps,
+                               cudaStream_t st);
 cudaError_t launch_eval_sparse(const DevInst &I, const int8_t *a, int nb, long long *cost,
                                cudaStream_t st);
 cudaError_t launch_round_pm1(const float *x, int8_t *a, long long count, cudaStream_t st);

@@ -58,7 +58,7 @@ class msat_info(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("steps_done", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("max_clause_len", ctypes.c_int32),
                 ("max_degree", ctypes.c_int32), ("n_heavy", ctypes.c_int32),
-                ("uniform_len", ctypes.c_int32)]
+                ("uniform_len", ctypes.c_int32), ("small_kernel", ctypes.c_int32)]
 
 
 class msat_server_config(ctypes.Structure):
@@ -96,6 +96,7 @@ class msat_profile(ctypes.Structure):
 
 STEP_NO_FINAL_EVAL = 1
 STEP_GRAPH = 2
+STEP_PER_PASS = 4
 PROFILE_KINDS = ("forward", "backward", "evaluate", "other")
 
 _lock = threading.Lock()

@@ -122,19 +122,22 @@ class Solver:
         check(self._lib.msat_set_stream(self._ctx, ctypes.c_void_p(st) if st else None))
 
     # -------------------------------------------------------------- loop
-    def step(self, n_steps: int, want_loss: bool = True, want_cost: bool = True, graph: bool = False
-             ) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
+    def step(self, n_steps: int, want_loss: bool = True, want_cost: bool = True, graph: bool = False,
+             per_pass: bool = False) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
         """n_steps iterations of Algorithm 1 plus a final evaluation; returns
         (loss at the last updated x, cost of the final x), each [B] or None.
-        graph: replay the steps from captured CUDA graphs (same bits)."""
+        graph: replay the steps from captured CUDA graphs; per_pass: keep a
+        small instance on the per-pass kernels (both give the same bits)."""
         loss = np.empty(self.B, np.float32) if want_loss else None
         cost = np.empty(self.B, np.int64) if want_cost else None
-        flags = native.STEP_GRAPH if graph else 0
+        flags = (native.STEP_GRAPH if graph else 0) | (native.STEP_PER_PASS if per_pass else 0)
         check(self._lib.msat_step_ex(self._ctx, int(n_steps), flags, _p(loss), _p(cost)))
         return loss, cost
 
-    def step_async(self, n_steps: int, final_eval: bool = True, graph: bool = False) -> None:
-        flags = (0 if final_eval else native.STEP_NO_FINAL_EVAL) | (native.STEP_GRAPH if graph else 0)
+    def step_async(self, n_steps: int, final_eval: bool = True, graph: bool = False,
+                   per_pass: bool = False) -> None:
+        flags = ((0 if final_eval else native.STEP_NO_FINAL_EVAL) | (native.STEP_GRAPH if graph else 0)
+                 | (native.STEP_PER_PASS if per_pass else 0))
         check(self._lib.msat_step_ex(self._ctx, int(n_steps), flags, None, None))
 
     def solve(self, max_steps: int, time_limit: float = float("inf"), chunk: int = 64,

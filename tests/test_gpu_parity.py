@@ -25,15 +25,17 @@ def pkg():
     return p
 
 
-def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, **kw):
-    """Cost after each evaluation (x_0 .. x_steps), loss of each update, final x."""
+def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, per_pass=True, **kw):
+    """Cost after each evaluation (x_0 .. x_steps), loss of each update, final
+    x.  per_pass: the per-pass kernels even for instances small enough for
+    the single-CTA kernel (False: whichever route msat_step takes)."""
     costs, losses = [], []
     with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=seed_x, lr=lr, **kw) as s:
         costs.append(s.step(0, want_loss=False)[1])
         done = 0
         while done < steps:
             k = min(chunk, steps - done)
-            loss, cost = s.step(k)
+            loss, cost = s.step(k, per_pass=per_pass)
             done += k
             costs.append(cost)
             losses.append(loss)
@@ -44,10 +46,11 @@ def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, **kw):
                 best_cost=best, info=info)
 
 
-def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, **kw):
+def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, per_pass=True, **kw):
     ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr,
                        loss_norm=kw.get("loss_norm", "mean_unsat"))
-    got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk, **kw)
+    got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk,
+                         per_pass=per_pass, **kw)
     idx = [0] + [min(k, steps) for k in range(chunk, steps + chunk, chunk)] if steps else [0]
     want_costs = ref["cost_hist"][idx]
     assert np.array_equal(got["cost_hist"], want_costs), "unsat cost history differs"
@@ -303,3 +306,41 @@ def test_heuristic_gap_matches_oracle(pkg, oracle, maker):
     f, sat = r["f"], r["unsat"] == 0
     assert np.array_equal(hu, (~(f > 0)).sum(axis=0))
     assert np.array_equal(dg, ((f > 0) != sat).sum(axis=0))
+
+
+# ---------------------------------------------- single-CTA small instances
+
+@pytest.mark.parametrize("case", ["config1", "weighted_zipf", "php40_long", "b64", "planted_stop",
+                                  "sum_unsat"])
+def test_small_instance_kernel_matches_oracle(pkg, oracle, case):
+    """The single-CTA kernel that runs every step of a small instance in one
+    launch: bit-exact trajectories against the oracle (chunks of steps, so
+    several launches continue one another), and its state continues on the
+    per-pass kernels with the same bits."""
+    kw = {}
+    if case == "config1":
+        cnf, B, S, lr, chunk = uniform_ksat(50, 215, 3, seed=0), 1, 300, 1e-2, 37
+    elif case == "weighted_zipf":
+        cnf, B, S, lr, chunk = zipf_weighted(700, 2800, seed=15), 4, 120, 1e-2, 50
+    elif case == "php40_long":
+        cnf, B, S, lr, chunk = pigeonhole(40), 1, 40, 1e-2, 13
+    elif case == "b64":
+        cnf, B, S, lr, chunk = uniform_ksat(80, 344, 3, seed=16), 64, 90, 3e-2, 30
+    elif case == "planted_stop":
+        cnf, B, S, lr, chunk = planted_ksat(60, 200, 3, seed=2), 16, 400, 5e-2, 100
+    else:
+        cnf, B, S, lr, chunk = uniform_ksat(200, 860, 3, seed=17), 8, 100, 1e-2, 25
+        kw["loss_norm"] = "sum_unsat"
+    with pkg.Solver.from_cnf(cnf, restarts=B, lr=lr, **kw) as s:
+        assert s.info()["small_kernel"] == 1
+    check_bit_exact(oracle, cnf, B, S, lr, chunk=chunk, per_pass=False, **kw)
+    # mixing the routes: small-kernel chunks, then per-pass steps
+    ref = oracle.solve(cnf, B, 1, S + 7, mode=oracle.MODE_F32, lr=lr,
+                       loss_norm=kw.get("loss_norm", "mean_unsat"))
+    with pkg.Solver.from_cnf(cnf, restarts=B, lr=lr, **kw) as s:
+        s.step(S, want_loss=False, want_cost=False)
+        s.step(7, want_loss=False, want_cost=False, per_pass=True)
+        x = s.x()
+        _, best = s.best()
+    assert np.array_equal(x.astype(np.float64), ref["x_final"])
+    assert np.array_equal(best, ref["best_cost"])
