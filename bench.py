@@ -275,6 +275,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     dense = args.workload in DENSE_EVAL
     dense_cost = torch.empty(B, dtype=torch.int64, device="cuda")
+    # small instances run every step of a call in one single-CTA launch:
+    # time one call of K steps (per-pass timing would force the per-pass
+    # kernels)
+    small = bool(solver.info()["small_kernel"]) and not dense
 
     def one_step():
         solver.step_async(1, final_eval=False)
@@ -295,27 +299,39 @@ def run_ours(args):
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    solver.profile(True)
-    solver.profile_read(reset=True)
+    if not small:
+        solver.profile(True)
+        solver.profile_read(reset=True)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
+    if small:
         if flush:
             flush_buf.zero_()
-        ev_s[k].record(stream)
-        one_step()
-        ev_e[k].record(stream)
+        ev_s[0].record(stream)
+        solver.step_async(args.steps, final_eval=False)
+        ev_e[0].record(stream)
+    else:
+        for k in range(args.steps):
+            if flush:
+                flush_buf.zero_()
+            ev_s[k].record(stream)
+            one_step()
+            ev_e[k].record(stream)
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    prof = solver.profile_read(reset=True)
-    solver.profile(False)
-    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
-    dev_ms = float(sum(step_ms))
+    if small:
+        dev_ms = float(ev_s[0].elapsed_time(ev_e[0]))
+        prof = {"forward": (0, 0.0), "backward": (0, 0.0), "evaluate": (0, 0.0), "other": (1, dev_ms)}
+    else:
+        prof = solver.profile_read(reset=True)
+        solver.profile(False)
+        step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+        dev_ms = float(sum(step_ms))
     from paper_2402_03640_gb300 import replicas
     t_max, units = replicas.combine(dev_ms, float(work_per_step * args.steps),
                                     device="cuda" if ws > 1 else None)
@@ -331,6 +347,14 @@ def run_ours(args):
             per_kernel[kind] = {"launches": launches, "avg_us": 1e3 * avg, "bound": "hbm",
                                 "bytes": abytes[kind], "gbs": abytes[kind] / (avg / 1e3) / 1e9,
                                 "frac": abytes[kind] / (avg / 1e3) / 1e9 / peak}
+    if small:
+        per_step = dev_ms / args.steps
+        by = abytes["forward"] + abytes["backward"]
+        per_kernel["small_steps"] = {"launches": 1, "steps_per_launch": args.steps,
+                                     "avg_us": 1e3 * per_step, "bound": "hbm", "bytes": by,
+                                     "gbs": by / (per_step / 1e3) / 1e9,
+                                     "frac": by / (per_step / 1e3) / 1e9 / peak}
+        abytes["small_steps"] = by
     if dense and prof["evaluate"][0]:
         launches, ms = prof["evaluate"]
         avg = ms / launches
@@ -400,8 +424,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "n": cnf.n, "m": cnf.m,
                    "nnz": nnz, "restarts": B, "lr": LR,
-                   "l2": ("flushed (256 MiB write) before every timed step" if flush
+                   "l2": ("flushed (256 MiB write) before the timed call, whose K steps run in one "
+                          "single-CTA launch with the state in shared memory" if small else
+                          "flushed (256 MiB write) before every timed step" if flush
                           else "working set larger than L2"),
+                   "route": "single-CTA kernel" if small else "per-pass kernels",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "n_heavy": info["n_heavy"]},
         "roofline": roofline,
@@ -594,7 +621,8 @@ def run_serving(args):
 
 KERNEL_SOURCES = {"forward": ("k_step.cu", "msat_internal.cuh"),
                   "backward": ("k_step.cu", "msat_internal.cuh"),
-                  "dense_eval": ("k_dense.cu", "msat_internal.cuh")}
+                  "dense_eval": ("k_dense.cu", "msat_internal.cuh"),
+                  "small_steps": ("k_step.cu", "msat_internal.cuh")}
 
 
 def kernel_hash(kind="forward"):

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "msat_internal.cuh"
 
 namespace msat {
@@ -1329,13 +1331,13 @@ __device__ __forceinline__ float small_clause_f(const DevInst &I, const float *_
 __global__ void __launch_bounds__(kSmallThreads, 1)
     k_small_steps(DevInst I, DevState S, DevStep D, int n_steps) {
     extern __shared__ float4 small_smem[];
-    __shared__ unsigned long long s_wu[kSmallMaxB];
     __shared__ float s_lsum[kSmallMaxB];
     __shared__ float s_lp[kSmallThreads];
+    __shared__ unsigned long long s_wp[kSmallThreads];
     __shared__ long long s_cost[kSmallMaxB], s_best[kSmallMaxB];
     __shared__ int s_imp[kSmallMaxB];
     __shared__ float s_cs[kSmallMaxB];
-    __shared__ float s_at, s_rt;
+    __shared__ float s_at, s_rt, s_at_next, s_rt_next;
     const int B = I.B;
     const int nB = I.n * B, mB = I.m * B;
     float *sx = reinterpret_cast<float *>(small_smem);
@@ -1353,15 +1355,26 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     const AdamView A0 = adam_view(sc);
     const int ln = sc->loss_norm;
     const long long wsum = sc->wsum;
-    double p1 = sc->p1, p2 = sc->p2;  // used by thread 0
+    // Adam scalars of each step from the running products, in double as the
+    // clause pass's last block computes them; the last thread computes the
+    // next step's while the others run the variable pass
+    double p1 = sc->p1, p2 = sc->p2;  // used by the last thread
+    double fin_p1 = p1, fin_p2 = p2;  // the products of the last step taken
+    float fin_at = 0.0f, fin_rt = 0.0f;
+    const int tl = blockDim.x - 1;
+    if (threadIdx.x == tl) {
+        p1 = p1 * sc->beta1;
+        p2 = p2 * sc->beta2;
+        s_at = (float)(sc->lr / (1.0 - p1));
+        s_rt = (float)(1.0 / sqrt(1.0 - p2));
+    }
     __syncthreads();
     for (int step = 0; step < n_steps; ++step) {
-        for (int b = threadIdx.x; b < B; b += blockDim.x) s_wu[b] = 0ull;
-        __syncthreads();
         // clause pass: f, exact unsat test, w*f (NaN where satisfied), sums.
         // The item stride (the block) is a multiple of B, so a thread keeps
         // one restart and its loss partial is one float.
         float lpart = 0.0f;
+        unsigned long long wpart = 0ull;
         for (int it = threadIdx.x; it < mB; it += blockDim.x) {
             const int j = it / B, b = it - j * B;
             bool sat;
@@ -1370,37 +1383,38 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
             if (!sat) {
                 const long long wj = I.w ? __ldg(I.w + j) : 1ll;
                 q = (float)wj * f;
-                atomicAdd(&s_wu[b], (unsigned long long)wj);
+                wpart += (unsigned long long)wj;
                 lpart += q * f;
             }
             sq[it] = q;
         }
         // loss partials in a fixed order: lanes of a restart by a shuffle
         // tree, then the warp partials in warp order
-        for (int o = B; o < 32; o <<= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
+        for (int o = B; o < 32; o <<= 1) {
+            lpart += __shfl_xor_sync(0xffffffffu, lpart, o);
+            wpart += __shfl_xor_sync(0xffffffffu, wpart, o);
+        }
         s_lp[threadIdx.x] = lpart;
+        s_wp[threadIdx.x] = wpart;
         __syncthreads();
+        // per-restart sums (integers exact in any order), then the scalars as
+        // the clause pass's last block computes them
         for (int b = threadIdx.x; b < B; b += blockDim.x) {
             const int stride = B < 32 ? 32 : B;
             float sum = 0.0f;
-            for (int k = b; k < kSmallThreads; k += stride) sum += s_lp[k];
+            unsigned long long wsm = 0ull;
+            for (int k = b; k < (int)blockDim.x; k += stride) {
+                sum += s_lp[k];
+                wsm += s_wp[k];
+            }
             s_lsum[b] = sum;
-        }
-        // per-restart scalars, as the clause pass's last block computes them
-        for (int b = threadIdx.x; b < B; b += blockDim.x) {
-            const long long c = (long long)s_wu[b];
+            const long long c = (long long)wsm;
             const int imp = c < s_best[b];
             if (imp) s_best[b] = c;
             s_cost[b] = c;
             s_imp[b] = imp;
             const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? wsum : c);
             s_cs[b] = c > 0 ? 2.0f / den : 0.0f;
-        }
-        if (threadIdx.x == 0) {
-            p1 = p1 * sc->beta1;
-            p2 = p2 * sc->beta2;
-            s_at = (float)(sc->lr / (1.0 - p1));
-            s_rt = (float)(1.0 / sqrt(1.0 - p2));
         }
         __syncthreads();
         AdamView A = A0;
@@ -1440,7 +1454,21 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
                 st[it] = tanh_fixed(xv);
             }
         }
+        if (threadIdx.x == tl) {  // the next step's scalars; read after the barrier
+            fin_p1 = p1;
+            fin_p2 = p2;
+            fin_at = A.a_t;
+            fin_rt = A.r_t;
+            p1 = p1 * sc->beta1;
+            p2 = p2 * sc->beta2;
+            s_at_next = (float)(sc->lr / (1.0 - p1));
+            s_rt_next = (float)(1.0 / sqrt(1.0 - p2));
+        }
         __syncthreads();
+        if (threadIdx.x == tl) {
+            s_at = s_at_next;
+            s_rt = s_rt_next;
+        }
     }
     // the state the per-pass kernels leave
     float *t_out = ((steps0 + n_steps) & 1) ? S.t1 : S.t0;
@@ -1461,14 +1489,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
         const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? wsum : c);
         D.loss[b] = c > 0 ? s_lsum[b] / den : 0.0f;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == tl) {
         long long tot = 0;
         for (int b = 0; b < B; ++b) tot += s_cost[b];
         sc->dense = (double)tot * 16.0 > (double)wsum * (double)B;
-        sc->p1 = p1;
-        sc->p2 = p2;
-        sc->a_t = s_at;
-        sc->r_t = s_rt;
+        sc->p1 = fin_p1;
+        sc->p2 = fin_p2;
+        sc->a_t = fin_at;
+        sc->r_t = fin_rt;
         sc->steps_done = steps0 + n_steps;
     }
 }
@@ -1489,7 +1517,12 @@ cudaError_t launch_small_steps(const DevInst &I, const DevState &S, const DevSte
     cudaError_t e = cudaFuncSetAttribute(k_small_steps, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmallSmemMax);
     if (e) return e;
-    k_small_steps<<<1, kSmallThreads, smem, st>>>(I, S, D, n_steps);
+    // a block of the work's size (a power of two, a multiple of B): the
+    // per-step barriers cost less with fewer warps
+    const long long items = std::max<long long>((long long)I.m * I.B, (long long)I.n * I.B);
+    int threads = 64;
+    while (threads < items && threads < kSmallThreads) threads <<= 1;
+    k_small_steps<<<1, threads, smem, st>>>(I, S, D, n_steps);
     return cudaGetLastError();
 }
 
