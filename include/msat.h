@@ -423,7 +423,10 @@ typedef struct {
 
 typedef struct {
     int64_t submitted, completed, failed, cancelled;
-    int32_t queued, running, peak_running, reserved;
+    int32_t queued, running, peak_running;
+    int32_t small_direct;  /* requests small enough for the single-CTA kernel: they
+                              take all their steps in one launch on a side stream
+                              as soon as they are admitted, outside the slot table */
     int64_t hbm_in_use, hbm_budget, rounds, graph_captures;
 } msat_server_stats;
 

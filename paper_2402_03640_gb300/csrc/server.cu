@@ -12,6 +12,10 @@
 // evaluated once more, its best costs and assignment are copied to pinned
 // host memory behind an event, and its memory is released in stream order
 // once the copy has landed; the freed budget admits queued requests.
+// An instance small enough for the single-CTA kernel (state in shared
+// memory) skips the slot table: it takes all its steps in one launch on one
+// of several side streams as soon as it is admitted and retires the same
+// way, so it is not held back by the large instances of the batch.
 //
 // Instances share no device state, so each result is bit for bit what the
 // same request gives alone through msat_create / msat_step / msat_best.
@@ -85,6 +89,10 @@ struct msat_server {
     msat_server_config cfg{};
     int device = 0;
     cudaStream_t compute = nullptr, admit = nullptr;
+    // small requests run apart from the slot table, round robin over these
+    static constexpr int kSmallStreams = 16;
+    cudaStream_t small_st[kSmallStreams] = {};
+    int small_next = 0;
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -164,6 +172,24 @@ void finish_failed(msat_server *S, uint64_t ticket, int code, Clock::time_point 
     S->cv_done.notify_all();
 }
 
+// Evaluate a finished instance once more and copy its best costs and
+// assignment to pinned host memory behind an event, all on the instance's
+// stream; reap() collects it when the event has completed.
+cudaError_t start_retire(msat_server *S, const SrvSlot &sl) {
+    msat_ctx *c = sl.ctx;
+    SrvFinishing fin;
+    fin.slot = sl;
+    cudaError_t e = ctx_eval_current(c);
+    if (!e) e = pinned_get(S, sizeof(int64_t) * (size_t)c->B, (void **)&fin.h_best, &fin.cap_best);
+    if (!e) e = pinned_get(S, (size_t)c->n * c->B, (void **)&fin.h_bits, &fin.cap_bits);
+    if (!e) e = cudaMemcpyAsync(fin.h_best, c->D.best, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(fin.h_bits, c->S.bestx, (size_t)c->n * c->B, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaEventCreateWithFlags(&fin.ev, cudaEventDisableTiming);
+    if (!e) e = cudaEventRecord(fin.ev, c->stream);
+    if (!e) S->finishing.push_back(fin);
+    return e;
+}
+
 void admit(msat_server *S, SrvRequest &req) {
     msat_config cfg;
     msat_config_default(&cfg);
@@ -183,7 +209,6 @@ void admit(msat_server *S, SrvRequest &req) {
         finish_failed(S, req.ticket, rc, req.t_submit);
         return;
     }
-    c->stream = S->compute;  // every later kernel of this instance runs on the compute stream
     SrvSlot sl;
     sl.ticket = req.ticket;
     sl.ctx = c;
@@ -193,6 +218,24 @@ void admit(msat_server *S, SrvRequest &req) {
     sl.t_admit = Clock::now();
     sl.bytes = (size_t)c->device_bytes;
     S->in_use += sl.bytes;
+    if (small_fits(c->I, c->max_deg)) {
+        // a small instance takes all its steps in one single-CTA launch on a
+        // side stream (same bits as the batched kernels), then retires
+        c->stream = S->small_st[S->small_next];
+        S->small_next = (S->small_next + 1) % msat_server::kSmallStreams;
+        cudaError_t e = launch_small_steps(c->I, c->S, c->D, req.steps, c->stream);
+        if (!e) e = start_retire(S, sl);
+        if (e) {
+            cuda_fail(e, "msat server: small instance");
+            finish_failed(S, req.ticket, MSAT_ECUDA, req.t_submit);
+            ctx_destroy_async(c);
+            S->in_use -= sl.bytes;
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->st.small_direct++;
+        return;
+    }
+    c->stream = S->compute;  // every later kernel of this instance runs on the compute stream
     S->slots.push_back(sl);
     S->dirty = true;
 }
@@ -287,18 +330,8 @@ int run_round(msat_server *S) {
             keep.push_back(sl);
             continue;
         }
-        msat_ctx *c = sl.ctx;
-        SrvFinishing fin;
-        fin.slot = sl;
-        cudaError_t e = ctx_eval_current(c);
-        if (!e) e = pinned_get(S, sizeof(int64_t) * (size_t)c->B, (void **)&fin.h_best, &fin.cap_best);
-        if (!e) e = pinned_get(S, (size_t)c->n * c->B, (void **)&fin.h_bits, &fin.cap_bits);
-        if (!e) e = cudaMemcpyAsync(fin.h_best, c->D.best, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost, S->compute);
-        if (!e) e = cudaMemcpyAsync(fin.h_bits, c->S.bestx, (size_t)c->n * c->B, cudaMemcpyDeviceToHost, S->compute);
-        if (!e) e = cudaEventCreateWithFlags(&fin.ev, cudaEventDisableTiming);
-        if (!e) e = cudaEventRecord(fin.ev, S->compute);
+        const cudaError_t e = start_retire(S, sl);
         if (e) return cuda_fail(e, "msat server: result copy");
-        S->finishing.push_back(fin);
         S->dirty = true;
     }
     S->slots.swap(keep);
@@ -437,6 +470,8 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     const int M = cfg.max_slots + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
     if (!e) e = cudaStreamCreateWithFlags(&S->admit, cudaStreamNonBlocking);
+    for (int k = 0; k < msat_server::kSmallStreams && !e; ++k)
+        e = cudaStreamCreateWithFlags(&S->small_st[k], cudaStreamNonBlocking);
     if (!e) e = cudaMalloc(&S->d_slots, sizeof(SlotDesc) * (size_t)cfg.max_slots);
     if (!e) e = cudaMalloc(&S->d_starts, sizeof(int) * 3 * (size_t)M);
     for (int k = 0; k < 2 && !e; ++k) {
@@ -474,6 +509,8 @@ extern "C" void msat_server_destroy(msat_server *S) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     if (S->compute) cudaStreamSynchronize(S->compute);
+    for (cudaStream_t st : S->small_st)
+        if (st) cudaStreamSynchronize(st);
     if (S->graph) cudaGraphExecDestroy(S->graph);
     cudaFree(S->d_slots);
     cudaFree(S->d_starts);
@@ -486,6 +523,8 @@ extern "C" void msat_server_destroy(msat_server *S) {
     for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
     if (S->compute) cudaStreamDestroy(S->compute);
     if (S->admit) cudaStreamDestroy(S->admit);
+    for (cudaStream_t st : S->small_st)
+        if (st) cudaStreamDestroy(st);
     delete S;
 }
 

@@ -85,7 +85,7 @@ class msat_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
                 ("queued", ctypes.c_int32), ("running", ctypes.c_int32),
-                ("peak_running", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("peak_running", ctypes.c_int32), ("small_direct", ctypes.c_int32),
                 ("hbm_in_use", ctypes.c_int64), ("hbm_budget", ctypes.c_int64),
                 ("rounds", ctypes.c_int64), ("graph_captures", ctypes.c_int64)]
 

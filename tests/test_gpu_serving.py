@@ -45,6 +45,7 @@ def test_mix_equals_alone(pkg, oracle, B):
         st = srv.stats()
     assert st["completed"] == len(mix) and st["failed"] == 0
     assert st["peak_running"] > 1  # requests really ran together
+    assert st["small_direct"] > 0  # and the small ones took the single-CTA route
     for (r, cnf), res in zip(mix, results):
         best, assign = _alone(pkg, cnf, B, steps, r.seed, lr)
         assert np.array_equal(res["best_costs"], best), r
