@@ -585,7 +585,8 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
     const float *__restrict__ t = t_ovr ? t_ovr : ((steps & 1) ? t1 : t0);
     const int kfix = KFIX > 0 ? KFIX : I.kfix;
     const int lane = threadIdx.x & 31;
-    const int g = threadIdx.x % G;
+    const int gshift = __ffs(G) - 1;  // G = B / VW is a power of two
+    const int g = threadIdx.x & (G - 1);
     const int col = g * VW;
     const long long total = (long long)I.m * G;
     const long long stride = (long long)nblk * blockDim.x;
@@ -607,7 +608,7 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
         for (int h = 0; h < NU; ++h) {
             item[h] = base + h * stride + lane;
             act[h] = item[h] < total;
-            jj[h] = act[h] ? (int)(item[h] / G) : 0;
+            jj[h] = act[h] ? (int)(item[h] >> gshift) : 0;
         }
         float f[NU][VW];
         bool sat[NU][VW];
