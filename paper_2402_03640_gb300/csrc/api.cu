@@ -695,6 +695,8 @@ extern "C" int msat_check(msat_ctx *c) {
     return MSAT_OK;
 }
 
+static int dense_eval(msat_ctx *c, const int8_t *a, const float *x, int32_t nb, int64_t *cost_out);
+
 extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
                              int32_t backend) {
     if (!c) return fail(MSAT_EINVAL, "msat_evaluate: ctx is NULL");
@@ -707,46 +709,53 @@ extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, 
         if (e) return cuda_fail(e, "msat_evaluate: sparse kernel");
         return MSAT_OK;
     }
-    if (backend == MSAT_BACKEND_DENSE) {
-        int rc = dense_setup(c);
-        if (rc) return rc;
-        const int rows = dense_rows(nb), ntile = dense_tile_n(nb);
-        const size_t need = (size_t)rows * c->dense.n_pad;
-        if (need > c->dense.xt_bytes) {
-            if (c->dense.Xt) {
-                cudaStreamSynchronize(c->stream);
-                cudaFree(c->dense.Xt);
-                c->dense.Xt = nullptr;
-                c->dense.xt_bytes = 0;
-            }
-            cudaError_t e = cudaMalloc(&c->dense.Xt, need);
-            if (e) {
-                cudaGetLastError();
-                c->dense.Xt = nullptr;
-                return fail(MSAT_ENOMEM, "msat_evaluate: dense assignment buffer allocation failed");
-            }
-            c->dense.xt_bytes = need;
-            c->dense.tmB_rows = 0;
-        }
-        if (c->dense.tmB_rows != rows || c->dense.tmB_ntile != ntile) {
-            rc = dense_encode_b(c->dense, rows, ntile);
-            if (rc) return rc;
-        }
-        prof_begin(c, PROF_OTHER);
-        cudaError_t e = launch_dense_convert(c->dense, assign_pm1, c->n, nb, (long long *)cost_out, c->stream);
-        prof_end(c);
-        if (e) return cuda_fail(e, "msat_evaluate: dense batch conversion");
-        prof_begin(c, PROF_EVAL);
-        e = launch_dense_gemm(c->dense, nb, (long long *)cost_out, c->stream);
-        prof_end(c);
-        if (e) return cuda_fail(e, "msat_evaluate: dense tensor-core kernel");
-        return MSAT_OK;
-    }
+    if (backend == MSAT_BACKEND_DENSE) return dense_eval(c, assign_pm1, nullptr, nb, cost_out);
     return fail(MSAT_EINVAL, "msat_evaluate: unknown backend");
+}
+
+// Tensor-core evaluation of a batch given as int8 +-1 (a) or as relaxed x
+// read through its rounding (x; the current x of the context).
+static int dense_eval(msat_ctx *c, const int8_t *a, const float *x, int32_t nb, int64_t *cost_out) {
+    int rc = dense_setup(c);
+    if (rc) return rc;
+    const int rows = dense_rows(nb), ntile = dense_tile_n(nb);
+    const size_t need = (size_t)rows * c->dense.n_pad;
+    if (need > c->dense.xt_bytes) {
+        if (c->dense.Xt) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->dense.Xt);
+            c->dense.Xt = nullptr;
+            c->dense.xt_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c->dense.Xt, need);
+        if (e) {
+            cudaGetLastError();
+            c->dense.Xt = nullptr;
+            return fail(MSAT_ENOMEM, "msat_evaluate: dense assignment buffer allocation failed");
+        }
+        c->dense.xt_bytes = need;
+        c->dense.tmB_rows = 0;
+    }
+    if (c->dense.tmB_rows != rows || c->dense.tmB_ntile != ntile) {
+        rc = dense_encode_b(c->dense, rows, ntile);
+        if (rc) return rc;
+    }
+    prof_begin(c, PROF_OTHER);
+    cudaError_t e = x ? launch_dense_convert_x(c->dense, x, c->n, nb, (long long *)cost_out, c->stream)
+                      : launch_dense_convert(c->dense, a, c->n, nb, (long long *)cost_out, c->stream);
+    prof_end(c);
+    if (e) return cuda_fail(e, "msat_evaluate: dense batch conversion");
+    prof_begin(c, PROF_EVAL);
+    e = launch_dense_gemm(c->dense, nb, (long long *)cost_out, c->stream);
+    prof_end(c);
+    if (e) return cuda_fail(e, "msat_evaluate: dense tensor-core kernel");
+    return MSAT_OK;
 }
 
 extern "C" int msat_evaluate_x(msat_ctx *c, int32_t backend, int64_t *cost_out) {
     if (!c || !cost_out) return fail(MSAT_EINVAL, "msat_evaluate_x: NULL argument");
+    // the tensor-core operand is built from x directly (rounding and transposition in one kernel)
+    if (backend == MSAT_BACKEND_DENSE) return dense_eval(c, nullptr, c->S.x, c->B, cost_out);
     const long long nB = (long long)c->n * c->B;
     if (!c->xpm1) {
         int rc = dalloc_t(c, &c->xpm1, (size_t)nB);

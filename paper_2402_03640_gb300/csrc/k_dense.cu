@@ -316,6 +316,25 @@ __global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uin
     }
 }
 
+// The same operand straight from the relaxed x (float [n][nb]): x > 0 reads
+// as +1, otherwise -1 -- the rounding of Sec. 4 -- without the int8 copy.
+__global__ void k_dense_convert_x(const float *__restrict__ x, int n, int nb, uint8_t *__restrict__ Xt,
+                                  int n_pad, int rows) {
+    __shared__ uint8_t tile[32][33];
+    const int v0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int v = v0 + r, b = b0 + threadIdx.x;
+        uint8_t e = 0;
+        if (v < n && b < nb) e = x[(long long)v * nb + b] > 0.0f ? kE4M3One : kE4M3MinusOne;
+        tile[r][threadIdx.x] = e;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r, v = v0 + threadIdx.x;
+        if (b < rows && v < n_pad) Xt[(long long)b * n_pad + v] = tile[threadIdx.x][r];
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -383,6 +402,15 @@ cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int 
                                  cudaStream_t st) {
     dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
     k_dense_convert<<<cg, cb, 0, st>>>(a, n, nb, d.Xt, d.n_pad, d.tmB_rows);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    return cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);
+}
+
+cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
+                                   cudaStream_t st) {
+    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
+    k_dense_convert_x<<<cg, cb, 0, st>>>(x, n, nb, d.Xt, d.n_pad, d.tmB_rows);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     return cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);

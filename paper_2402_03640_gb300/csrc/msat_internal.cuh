@@ -267,6 +267,8 @@ int dense_encode_b(DenseDev &d, int rows, int ntile);
 cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStream_t st);
 cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
                                  cudaStream_t st);
+cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
+                                   cudaStream_t st);
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st);
 
 }  // namespace msat
