@@ -319,9 +319,11 @@ __global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uin
 // The same operand straight from the relaxed x (float [n][nb]): x > 0 reads
 // as +1, otherwise -1 -- the rounding of Sec. 4 -- without the int8 copy.
 __global__ void k_dense_convert_x(const float *__restrict__ x, int n, int nb, uint8_t *__restrict__ Xt,
-                                  int n_pad, int rows) {
+                                  int n_pad, int rows, long long *__restrict__ cost) {
     __shared__ uint8_t tile[32][33];
     const int v0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    if (blockIdx.x == 0 && blockIdx.y == 0)  // the GEMM that follows in stream order adds into cost
+        for (int b = threadIdx.y * 32 + threadIdx.x; b < nb; b += 32 * blockDim.y) cost[b] = 0;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int v = v0 + r, b = b0 + threadIdx.x;
         uint8_t e = 0;
@@ -410,10 +412,8 @@ cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int 
 cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
                                    cudaStream_t st) {
     dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
-    k_dense_convert_x<<<cg, cb, 0, st>>>(x, n, nb, d.Xt, d.n_pad, d.tmB_rows);
-    cudaError_t e = cudaGetLastError();
-    if (e) return e;
-    return cudaMemsetAsync(cost, 0, sizeof(long long) * (size_t)nb, st);
+    k_dense_convert_x<<<cg, cb, 0, st>>>(x, n, nb, d.Xt, d.n_pad, d.tmB_rows, cost);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st) {

@@ -1059,13 +1059,16 @@ __device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, c
     const bool dense = D.sc->dense != 0;
     const bool expanded = KFIX == 3 && I.occx != nullptr;
 
+    const bool one_leaf_each = nleaves == nv;  // uniform: task ti belongs to variable ti
     for (int t = threadIdx.x; t < ntasks; t += kThreads) {
         const int ti = t >> gshift;
         int lo = 0, hi = nv - 1;  // the variable: last vloc with s_lpre[vloc] <= ti
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_lpre[mid] <= ti) lo = mid; else hi = mid - 1;
-        }
+        if (one_leaf_each) lo = ti;
+        else
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_lpre[mid] <= ti) lo = mid; else hi = mid - 1;
+            }
         const int vloc = lo;
         const int L = ti - s_lpre[vloc];
         const int nleaf = s_lpre[vloc + 1] - s_lpre[vloc];
