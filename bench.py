@@ -394,6 +394,8 @@ def run_ours(args):
     s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
     for _ in range(e2e_steps):
         s2.step(1)
+        if dense:  # the same step as the timed one: the tensor-core evaluation too
+            _ = s2.evaluate_x("dense").cpu().numpy()
     t1 = time.perf_counter()
     s2.close()
     e_max, e_units = replicas.combine(t1 - t0, float(work_per_step * e2e_steps),
@@ -436,9 +438,11 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "literal-evals/s", "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": B * (4 + 8),
+                "d2h_bytes_per_step": B * (4 + 8) + (B * 8 if dense else 0),
                 "note": "msat_create from host arrays once, then per step msat_step(1) with the "
-                        "loss and cost copied back to host buffers"},
+                        "loss and cost copied back to host buffers" +
+                        (", and msat_evaluate_x on the tensor cores with its costs copied back"
+                         if dense else "")},
         "gpu_launches": launches,
         "wall_s_timed": wall1 - wall0,
         "final_cost_min": int(cost.min()),
