@@ -251,6 +251,19 @@ int msat_evaluate_x(msat_ctx *ctx, int32_t backend, int64_t *cost_out);
 int msat_check(msat_ctx *ctx);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper).  Every device
+ * wait of this library (the mbarrier phases of the tensor-core evaluator)
+ * gives up after a bounded number of tries, records the reason in an error
+ * flag and returns, so a phase that never completes is reported by
+ * msat_check as MSAT_ETIMEOUT instead of hanging the GPU.  This call runs
+ * that path on purpose: one thread waits `spins` tries (1 .. 2^24) on a
+ * barrier nothing arrives at.  Returns MSAT_ETIMEOUT (the expected result)
+ * with the flag in the message; the device stays usable.  Synchronous;
+ * allocates and frees one 4-byte flag.
+ */
+int msat_selftest_bounded_wait(int64_t spins);
+
+/*
  * The paper's quick evaluation reads clause j as satisfied when f_j > 0
  * (Sec. 4, "Example": a positive clause value marks a satisfied clause);
  * the exact test is "some literal is true under x > 0" (Sec. 4,

@@ -36,6 +36,15 @@ using namespace msat;
 
 #include "ctx.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over a host call (visible to nsys / ncu --nvtx; no cost
+// without an attached tool)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 enum { PROF_FWD = 0, PROF_BWD = 1, PROF_EVAL = 2, PROF_OTHER = 3 };
 
 static void prof_begin(msat_ctx *c, int kind) {
@@ -547,6 +556,7 @@ extern "C" int msat_step_ex(msat_ctx *c, int32_t n_steps, uint32_t flags, float 
     if (n_steps < 0) return fail(MSAT_EINVAL, "msat_step: n_steps < 0");
     if (flags & ~(MSAT_STEP_NO_FINAL_EVAL | MSAT_STEP_GRAPH | MSAT_STEP_PER_PASS))
         return fail(MSAT_EINVAL, "msat_step: unknown flags");
+    NvtxRange nv("msat_step");
     cudaError_t e = run_steps(c, n_steps, flags);
     if (!e && !(flags & MSAT_STEP_NO_FINAL_EVAL)) e = eval_current(c);
     if (e) return cuda_fail(e, "msat_step: kernel launch");
@@ -574,6 +584,7 @@ extern "C" int msat_solve(msat_ctx *c, int64_t max_steps, double time_limit_s, i
                                  "time_limit_s >= 0 required");
     if (trace_cap > 0 && (!trace_cost || !trace_time))
         return fail(MSAT_EINVAL, "msat_solve: trace buffers are NULL");
+    NvtxRange nv("msat_solve");
     const auto t0 = std::chrono::steady_clock::now();
     auto seconds = [&] {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -716,6 +727,7 @@ extern "C" int msat_evaluate(msat_ctx *c, const int8_t *assign_pm1, int32_t nb, 
 // Tensor-core evaluation of a batch given as int8 +-1 (a) or as relaxed x
 // read through its rounding (x; the current x of the context).
 static int dense_eval(msat_ctx *c, const int8_t *a, const float *x, int32_t nb, int64_t *cost_out) {
+    NvtxRange nv("msat_evaluate dense");
     int rc = dense_setup(c);
     if (rc) return rc;
     const int rows = dense_rows(nb), ntile = dense_tile_n(nb);
@@ -943,5 +955,22 @@ extern "C" int msat_backward(msat_ctx *c, const float *gscale, float *grad) {
     cudaError_t e = launch_backward(c->I, c->PS, c->PD, BWD_GRAD_ONLY, c->PS.t0, gscale, grad,
                                     c->stream);
     if (e) return cuda_fail(e, "msat_backward");
+    return MSAT_OK;
+}
+
+extern "C" int msat_selftest_bounded_wait(int64_t spins) {
+    if (spins < 1 || spins > (1LL << 24))
+        return fail(MSAT_EINVAL, "msat_selftest_bounded_wait: spins must be in [1, 2^24]");
+    unsigned int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(unsigned));
+    if (e) return cuda_fail(e, "msat_selftest_bounded_wait: allocation");
+    unsigned h = 0;
+    e = cudaMemset(flag, 0, sizeof(unsigned));
+    if (!e) e = launch_wait_selftest(spins, flag, nullptr);
+    if (!e) e = cudaMemcpy(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e) return cuda_fail(e, "msat_selftest_bounded_wait");
+    if (h) return fail(MSAT_ETIMEOUT, "msat_selftest_bounded_wait: the wait gave up after " +
+                                          std::to_string(spins) + " tries (flag " + std::to_string(h) + ")");
     return MSAT_OK;
 }

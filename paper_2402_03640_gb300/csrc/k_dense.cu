@@ -275,6 +275,19 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that
+// nothing arrives at, gives up after `spins` tries and records it in the
+// error flag -- the path every wait of k_dense_eval takes when a phase never
+// completes.  Nothing faults and nothing hangs; the context stays usable.
+__global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0u, spins)) atomicOr(errflag, 8u);
+    }
+}
+
 // W^T in e4m3: row j holds +1 / -1 at the columns of the clause's literals
 // (the buffer was zeroed).  A clause with x and not x writes both; its target
 // is NaN, so it never counts.
@@ -432,5 +445,10 @@ cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaSt
 }
 
 size_t smem_max_dense() { return dense_smem_bytes(256); }
+
+cudaError_t launch_wait_selftest(long long spins, unsigned int *errflag, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(spins, errflag);
+    return cudaGetLastError();
+}
 
 }  // namespace msat

@@ -270,5 +270,6 @@ cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int 
 cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
                                    cudaStream_t st);
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st);
+cudaError_t launch_wait_selftest(long long spins, unsigned int *errflag, cudaStream_t st);
 
 }  // namespace msat

@@ -35,6 +35,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ctx.cuh"
 
 using namespace msat;
@@ -301,7 +303,7 @@ int rebuild(msat_server *S) {
 
 // One scheduling round: advance every slot by R steps, then retire the
 // slots that have taken all their steps.
-int run_round(msat_server *S) {
+int run_round_body(msat_server *S) {
     if (S->dirty) {
         const int rc = rebuild(S);
         if (rc) return rc;
@@ -336,6 +338,13 @@ int run_round(msat_server *S) {
     }
     S->slots.swap(keep);
     return MSAT_OK;
+}
+
+int run_round(msat_server *S) {
+    nvtxRangePushA("msat server round");
+    const int rc = run_round_body(S);
+    nvtxRangePop();
+    return rc;
 }
 
 // Collect finished results (waiting for the first one when block is set).
