@@ -283,6 +283,15 @@ int msat_heuristic_gap(msat_ctx *ctx, int64_t *heur_unsat, int64_t *disagree);
  */
 int msat_best(msat_ctx *ctx, uint8_t *assign01, int64_t *best_cost);
 
+/*
+ * Steps to best (Alg. 1 lines 5-7 keep the best assignment; this reports when
+ * it was found): for each restart, the number of optimizer steps taken before
+ * the x whose cost is the best cost (0: the random start x_0), an index of
+ * the cost-vs-step history.  Not part of a checkpoint: reads 0 after
+ * msat_set_state.  best_step host int64[B]; synchronous.
+ */
+int msat_best_step(msat_ctx *ctx, int64_t *best_step);
+
 /* Copy the current relaxed variables to host float[n][B] (entry i*B + b). */
 int msat_get_x(msat_ctx *ctx, float *x_host);
 
@@ -432,6 +441,8 @@ typedef struct {
     int32_t restarts;
     double queue_ms;      /* submit -> admitted                          */
     double latency_ms;    /* submit -> result ready                      */
+    int64_t best_step;    /* steps taken before the best restart's best x
+                             (steps to best; 0 = the random start)        */
 } msat_result;
 
 typedef struct {

@@ -391,6 +391,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     TRY_ALLOC(D.wu_acc, (int64_t)kRep * B);
     TRY_ALLOC(D.cost, B);
     TRY_ALLOC(D.best, B);
+    TRY_ALLOC(D.best_step, B);
     TRY_ALLOC(D.improved, B);
     TRY_ALLOC(D.cscale, B);
     TRY_ALLOC(D.loss, B);
@@ -434,6 +435,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (!e && expand) e = up(d_occx, occx.data(), sizeof(int2) * occx.size());
     if (!e) e = up(D.sc, &sc, sizeof(sc));
     if (!e) e = up(D.best, best.data(), sizeof(long long) * best.size());
+    if (!e) e = cudaMemsetAsync(D.best_step, 0, sizeof(long long) * (size_t)B, st);
     if (!e) e = cudaMemsetAsync(D.wu_acc, 0, sizeof(unsigned long long) * (size_t)kRep * B, st);
     if (!e) e = cudaMemsetAsync(D.improved, 0, sizeof(int) * (size_t)B, st);
     if (!e) e = cudaMemsetAsync(D.cost, 0, sizeof(long long) * (size_t)B, st);
@@ -886,6 +888,8 @@ extern "C" int msat_set_state(msat_ctx *c, const float *x, const float *mom, con
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.x, x, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.mom, mom, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.vel, vel, sizeof(float) * nB, cudaMemcpyHostToDevice, st));
+    // the step of a restored best is not part of a checkpoint: it reads 0 after a restore
+    MSAT_CUDA_TRY(cudaMemsetAsync(c->D.best_step, 0, sizeof(int64_t) * (size_t)c->B, st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->D.best, best_cost, sizeof(int64_t) * (size_t)c->B,
                                   cudaMemcpyHostToDevice, st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(c->S.bestx, best_assign, nB, cudaMemcpyHostToDevice, st));
@@ -917,6 +921,7 @@ static int ensure_probe(msat_ctx *c) {
     if ((rc = dalloc_t(c, &c->PD.cscale, B))) return rc;
     if ((rc = dalloc_t(c, &c->PD.lpart, (int64_t)c->PD.fwd_blocks * B))) return rc;
     c->PD.best = nullptr;
+    c->PD.best_step = nullptr;
     c->PD.improved = nullptr;
     StepScalars sc;
     MSAT_CUDA_TRY(cudaMemcpyAsync(&sc, c->D.sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
@@ -972,5 +977,13 @@ extern "C" int msat_selftest_bounded_wait(int64_t spins) {
     if (e) return cuda_fail(e, "msat_selftest_bounded_wait");
     if (h) return fail(MSAT_ETIMEOUT, "msat_selftest_bounded_wait: the wait gave up after " +
                                           std::to_string(spins) + " tries (flag " + std::to_string(h) + ")");
+    return MSAT_OK;
+}
+
+extern "C" int msat_best_step(msat_ctx *c, int64_t *best_step) {
+    if (!c || !best_step) return fail(MSAT_EINVAL, "msat_best_step: NULL argument");
+    MSAT_CUDA_TRY(cudaMemcpyAsync(best_step, c->D.best_step, sizeof(int64_t) * (size_t)c->B,
+                                  cudaMemcpyDeviceToHost, c->stream));
+    MSAT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return MSAT_OK;
 }

@@ -725,7 +725,10 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
         if (mode != FWD_PROBE) {
             const long long bb = D.best[b];
             const int imp = c < bb;
-            if (imp) D.best[b] = c;
+            if (imp) {
+                D.best[b] = c;
+                D.best_step[b] = steps;
+            }
             D.improved[b] = imp;
         }
         // g_j = (w_j f_j) * 2 / N with N = W_U (mean over the unsat clauses),
@@ -1338,7 +1341,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     __shared__ float s_lsum[kSmallMaxB];
     __shared__ float s_lp[kSmallThreads];
     __shared__ unsigned long long s_wp[kSmallThreads];
-    __shared__ long long s_cost[kSmallMaxB], s_best[kSmallMaxB];
+    __shared__ long long s_cost[kSmallMaxB], s_best[kSmallMaxB], s_bstep[kSmallMaxB];
     __shared__ int s_imp[kSmallMaxB];
     __shared__ float s_cs[kSmallMaxB];
     __shared__ float s_at, s_rt, s_at_next, s_rt_next;
@@ -1355,7 +1358,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
         sve[q] = S.vel[q];
         st[q] = t_in[q];
     }
-    for (int b = threadIdx.x; b < B; b += blockDim.x) s_best[b] = D.best[b];
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        s_best[b] = D.best[b];
+        s_bstep[b] = D.best_step[b];
+    }
     const AdamView A0 = adam_view(sc);
     const int ln = sc->loss_norm;
     const long long wsum = sc->wsum;
@@ -1414,7 +1420,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
             s_lsum[b] = sum;
             const long long c = (long long)wsm;
             const int imp = c < s_best[b];
-            if (imp) s_best[b] = c;
+            if (imp) {
+                s_best[b] = c;
+                s_bstep[b] = steps0 + step;
+            }
             s_cost[b] = c;
             s_imp[b] = imp;
             const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? wsum : c);
@@ -1487,6 +1496,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         D.cost[b] = s_cost[b];
         D.best[b] = s_best[b];
+        D.best_step[b] = s_bstep[b];
         D.improved[b] = s_imp[b];
         D.cscale[b] = s_cs[b];
         const long long c = s_cost[b];

@@ -75,6 +75,7 @@ struct DevStep {
     unsigned long long *wu_acc;  // [kRep][B] atomic accumulators of sum_U w
     long long *cost;             // [B] cost of the evaluated x
     long long *best;             // [B] best cost so far
+    long long *best_step;        // [B] updates taken before the x that gave it (0: x_0)
     int *improved;               // [B] cost < best at the last evaluation
     float *cscale;               // [B] 2 / (float)W_U (0 if W_U = 0)
     float *loss;                 // [B] loss of the last updated x

@@ -69,7 +69,8 @@ struct SrvFinishing {
     cudaEvent_t ev = nullptr;
     int64_t *h_best = nullptr;  // pinned [B]
     uint8_t *h_bits = nullptr;  // pinned [n][B]
-    size_t cap_best = 0, cap_bits = 0;
+    int64_t *h_bstep = nullptr; // pinned [B]
+    size_t cap_best = 0, cap_bits = 0, cap_bstep = 0;
 };
 
 struct SrvDone {
@@ -184,6 +185,8 @@ cudaError_t start_retire(msat_server *S, const SrvSlot &sl) {
     cudaError_t e = ctx_eval_current(c);
     if (!e) e = pinned_get(S, sizeof(int64_t) * (size_t)c->B, (void **)&fin.h_best, &fin.cap_best);
     if (!e) e = pinned_get(S, (size_t)c->n * c->B, (void **)&fin.h_bits, &fin.cap_bits);
+    if (!e) e = pinned_get(S, sizeof(int64_t) * (size_t)c->B, (void **)&fin.h_bstep, &fin.cap_bstep);
+    if (!e) e = cudaMemcpyAsync(fin.h_bstep, c->D.best_step, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(fin.h_best, c->D.best, sizeof(int64_t) * (size_t)c->B, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(fin.h_bits, c->S.bestx, (size_t)c->n * c->B, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaEventCreateWithFlags(&fin.ev, cudaEventDisableTiming);
@@ -373,6 +376,7 @@ void reap(msat_server *S, bool block) {
         d.res.status = 0;
         d.res.best_restart = bb;
         d.res.best_cost = d.best[(size_t)bb];
+        d.res.best_step = f.h_bstep[bb];
         d.res.steps = f.slot.steps;
         d.res.n_vars = n;
         d.res.restarts = B;
@@ -382,6 +386,7 @@ void reap(msat_server *S, bool block) {
         S->in_use -= f.slot.bytes;
         pinned_put(S, f.h_best, f.cap_best);
         pinned_put(S, f.h_bits, f.cap_bits);
+        pinned_put(S, f.h_bstep, f.cap_bstep);
         cudaEventDestroy(f.ev);
         {
             std::lock_guard<std::mutex> lk(S->mu);

@@ -78,7 +78,8 @@ class msat_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("best_restart", ctypes.c_int32),
                 ("best_cost", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("n_vars", ctypes.c_int32), ("restarts", ctypes.c_int32),
-                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("best_step", ctypes.c_int64)]
 
 
 class msat_server_stats(ctypes.Structure):
@@ -141,6 +142,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_autotune": ([i32, i64, P, P, P, P, P, i32, P, P, i32, P], ctypes.c_int),
             "msat_heuristic_gap": ([P, P, P], ctypes.c_int),
             "msat_selftest_bounded_wait": ([i64], ctypes.c_int),
+            "msat_best_step": ([P, P], ctypes.c_int),
             "msat_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
             "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),
             "msat_objective_noalloc": ([i32, i64, P, P, P, P, i32, P, P, P], ctypes.c_int),

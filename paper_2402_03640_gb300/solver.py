@@ -221,6 +221,13 @@ class Solver:
         check(self._lib.msat_evaluate(self._ctx, _p(a), nb, _p(out), be))
         return out
 
+    def best_step(self) -> np.ndarray:
+        """Per restart, the optimizer steps taken before the x that gave the
+        best cost (0: the random start)."""
+        out = np.empty(self.B, np.int64)
+        check(self._lib.msat_best_step(self._ctx, _p(out)))
+        return out
+
     def heuristic_gap(self) -> Tuple[np.ndarray, np.ndarray]:
         """(clauses the quick f_j > 0 reading calls unsat, clauses on which it
         disagrees with the exact test), each int64 [B], at the current x."""

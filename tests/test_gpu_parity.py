@@ -344,3 +344,18 @@ def test_small_instance_kernel_matches_oracle(pkg, oracle, case):
         _, best = s.best()
     assert np.array_equal(x.astype(np.float64), ref["x_final"])
     assert np.array_equal(best, ref["best_cost"])
+
+
+@pytest.mark.parametrize("per_pass", [True, False])
+def test_best_step_is_first_minimum_of_cost_history(pkg, oracle, per_pass):
+    """Steps to best: for each restart, the first step index at which the
+    oracle's cost history reaches its minimum (strict improvement keeps the
+    first), on the per-pass kernels and on the single-CTA route."""
+    cnf = uniform_ksat(300, 1290, 3, seed=18)
+    B, S, lr = 8, 150, 2e-2
+    ref = oracle.solve(cnf, B, 1, S, mode=oracle.MODE_F32, lr=lr)
+    want = np.argmin(ref["cost_hist"], axis=0)
+    with pkg.Solver.from_cnf(cnf, restarts=B, lr=lr) as s:
+        s.step(S, want_loss=False, want_cost=False, per_pass=per_pass)
+        assert np.array_equal(s.best_step(), want)
+        assert np.array_equal(s.best()[1], ref["best_cost"])

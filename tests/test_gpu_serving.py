@@ -23,11 +23,12 @@ def pkg():
     return p
 
 
-def _alone(pkg, cnf, B, steps, seed, lr):
+def _alone(pkg, cnf, B, steps, seed, lr, with_step=False):
     with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=seed, lr=lr) as s:
         s.step(steps, want_loss=False, want_cost=False)
         assign, best = s.best()
-    return best, assign
+        bstep = s.best_step()
+    return (best, assign, bstep) if with_step else (best, assign)
 
 
 def _mix(seed=0, count=24):
@@ -47,10 +48,12 @@ def test_mix_equals_alone(pkg, oracle, B):
     assert st["peak_running"] > 1  # requests really ran together
     assert st["small_direct"] > 0  # and the small ones took the single-CTA route
     for (r, cnf), res in zip(mix, results):
-        best, assign = _alone(pkg, cnf, B, steps, r.seed, lr)
+        best, assign, bstep = _alone(pkg, cnf, B, steps, r.seed, lr, with_step=True)
         assert np.array_equal(res["best_costs"], best), r
         assert np.array_equal(res["assignment"], assign[res["best_restart"]])
         assert res["best_cost"] == best.min() and res["steps"] == steps
+        # steps to best of the best restart, as the same request alone reports it
+        assert res["best_step"] == bstep[res["best_restart"]]
     # a few against the oracle directly
     for (r, cnf), res in list(zip(mix, results))[:3]:
         ref = oracle.solve(cnf, B, r.seed, steps, mode=oracle.MODE_F32, lr=lr, want_hist=False)
