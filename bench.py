@@ -63,7 +63,11 @@ LR = 1e-4
 
 
 def algorithmic_bytes(cnf, B):
-    """Minimum bytes each kernel must move per launch."""
+    """Minimum bytes each pass must move per launch.  Clause pass: the
+    literal stream (4 nnz), each t value once (4 n B), the unsat bits
+    (m B / 8), plus clause offsets when lengths differ and the weights.
+    Variable pass: occurrence offsets and lists (4 (n+1) + 4 nnz), the unsat
+    bits, x, m and v read and written (24 n B) and t written (4 n B)."""
     n, m, nnz = cnf.n, cnf.m, cnf.nnz
     lens = np.diff(cnf.off)
     uniform = m > 0 and bool(np.all(lens == lens[0]))
