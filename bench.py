@@ -275,7 +275,8 @@ def run_ours(args):
     flush = working_set < 2 * L2_BYTES
     flush_buf = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda") if flush else None
 
-    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
+    # launch shapes from the library's autotuner (they never change a result bit)
+    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, tune=True)
     stream = torch.cuda.current_stream()
     dense = args.workload in DENSE_EVAL
     dense_cost = torch.empty(B, dtype=torch.int64, device="cuda")
@@ -490,6 +491,7 @@ def run_ours(args):
                         (", and msat_evaluate_x on the tensor cores with its costs copied back"
                          if dense else "")},
         "gpu_launches": launches,
+        "tuned_shape": solver.tuning and {k: solver.tuning[k] for k in ("fwd_vw", "stage_vw", "light_rows")},
         "wall_s_timed": wall1 - wall0,
         "final_cost_min": int(cost.min()),
         "dense_eval_matches_sparse": dense_ok,
