@@ -12,7 +12,7 @@
  *   f_j = sum over literals of c_j of (+t_i for x_i, -t_i for not x_i)
  *   x'_i = [x_i > 0];  clause j is unsat iff no literal is true under x'
  *   cost = sum of w_j over unsat clauses  (exact integer)
- *   best cost / best assignment kept (Alg. 1 lines 5-7)
+ *   best cost / best assignment kept (Alg. 1)
  *   L = sum_{unsat j} w_j f_j^2 / sum_{unsat j} w_j    (masked MSE)
  *   gradient by backpropagation, one Adam step (Sec. 5)
  *   a restart whose cost reaches 0 stops (Alg. 1 stop rule)
@@ -72,7 +72,7 @@ typedef struct {
                          MSAT_F_RECOMPUTE (recomputed from the clause CSR),
                          MSAT_F_EXPANDED (3-literal clauses: recomputed from
                          occurrence records holding the other two literals) */
-    uint64_t seed_x;  /* seed of the random start of x (Alg. 1 line 1)         */
+    uint64_t seed_x;  /* seed of the random start of x (Alg. 1)                 */
     int32_t heavy_deg; /* occurrences above which a variable's sum is split
                           into 1024-occurrence chunks (0 = automatic)          */
     /* Launch shapes (0 = automatic).  None of them changes a result bit: the
@@ -110,7 +110,7 @@ typedef struct {
 int msat_config_default(msat_config *cfg);
 
 /*
- * Build a solver context for one CNF (Alg. 1 line 1: "construct W").
+ * Build a solver context for one CNF (Alg. 1: the clause matrix is built once).
  *   n_vars      n >= 1 (variables are numbered 1..n in lits)
  *   n_clauses   m >= 0
  *   clause_off  host int64[m+1], clause j holds lits[clause_off[j] ..
@@ -172,9 +172,8 @@ int msat_step_ex(msat_ctx *ctx, int32_t n_steps, uint32_t flags, float *loss_out
                  int64_t *cost_out);
 
 /*
- * Time-limited solving: Algorithm 1 with its wall-clock limit T (Sec. 4,
- * Algorithm 1 input "time limit"; the loop ends at zero cost or when T is
- * reached).  Runs the steps in chunks of `chunk` steps (CUDA-graph replays
+ * Time-limited solving (Sec. 4: Algorithm 1 takes a wall-clock limit T as
+ * input and ends at zero cost or when T is reached).  Runs the steps in chunks of `chunk` steps (CUDA-graph replays
  * unless kernel timing is on) until some restart's best cost is 0,
  * max_steps steps have run, or time_limit_s seconds have passed (checked
  * after each chunk, so a chunk in flight completes); then evaluates the
@@ -277,14 +276,14 @@ int msat_selftest_bounded_wait(int64_t spins);
 int msat_heuristic_gap(msat_ctx *ctx, int64_t *heur_unsat, int64_t *disagree);
 
 /*
- * Best assignment and cost seen so far per restart (Alg. 1 lines 5-7).
+ * Best assignment and cost seen so far per restart (Alg. 1, best kept).
  *   assign01   host uint8[B][n] (0/1), or NULL
  *   best_cost  host int64[B], or NULL
  */
 int msat_best(msat_ctx *ctx, uint8_t *assign01, int64_t *best_cost);
 
 /*
- * Steps to best (Alg. 1 lines 5-7 keep the best assignment; this reports when
+ * Steps to best (Alg. 1 keeps the best assignment; this reports when
  * it was found): for each restart, the number of optimizer steps taken before
  * the x whose cost is the best cost (0: the random start x_0), an index of
  * the cost-vs-step history.  Not part of a checkpoint: reads 0 after

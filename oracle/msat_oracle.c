@@ -539,10 +539,10 @@ static void adam_scalars(const orc_adam *h, int64_t t, float *a_t, float *r_t)
 /*
  * One iteration of Algorithm 1 in FP32-canon arithmetic, on the state
  * (x, mom, vel) [n][B] with `steps_done` optimizer steps already taken:
- *   evaluate x (cost, loss)            Alg. 1 lines 3-4
- *   best update (strict <)             lines 5-7
- *   if cost == 0 the restart has stopped: no update (line 2 stop rule)
- *   else gradient + one Adam step      lines 8-9
+ *   evaluate x (cost, loss)            Algorithm 1, evaluation
+ *   best update (strict <)             Algorithm 1, best kept
+ *   if cost == 0 the restart has stopped: no update (Algorithm 1 stops at zero)
+ *   else gradient + one Adam step      Algorithm 1, backpropagation and update
  * If `update` is 0 only the evaluation and best update run (the final
  * evaluation after the last step).  best_assign may be NULL.
  */
@@ -621,7 +621,7 @@ int orc_solve(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, con
     const int64_t nb = (int64_t)n * B;
     int64_t wsum = 0;
     for (int64_t j = 0; j < c.m; ++j) wsum += c.w[j];
-    for (int32_t b = 0; b < B; ++b) best_cost[b] = wsum; /* Alg. 1 line 1 */
+    for (int32_t b = 0; b < B; ++b) best_cost[b] = wsum; /* Algorithm 1 starts from the total weight */
     int64_t *cost = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
     double *loss = (double *)malloc(sizeof(double) * (size_t)B);
     float *x0 = (float *)malloc(sizeof(float) * (size_t)(nb + 1));

@@ -114,7 +114,7 @@ def splitmix64(seed: int, c: int) -> int:
 
 
 def init_x(n: int, B: int, seed: int) -> np.ndarray:
-    """Random start of Algorithm 1 line 1: float32 [n][B] on the grid of [-1, 1)."""
+    """Random start of Algorithm 1: float32 [n][B] on the grid of [-1, 1)."""
     x = np.empty((n, B), dtype=np.float32)
     _check(_load().orc_init_x(n, B, seed, _p(x)), "init_x")
     return x

@@ -1,6 +1,6 @@
 // Step kernels of the MaxSAT gradient engine (sm_103a).
 //
-//   k_init            random start of x (Alg. 1 line 1), zero Adam moments,
+//   k_init            random start of x (Algorithm 1 initialisation), zero Adam moments,
 //                     tanh(x)
 //   k_forward         clause pass: f_j, exact unsat bits, sum_U w and the
 //                     loss partials per restart; the last block to finish
