@@ -82,7 +82,7 @@ def algorithmic_bytes(cnf, B):
 
 def measured_peaks():
     """(HBM GB/s, source), (fp8 dense TFLOP/s, source): the copy bandwidth and
-    the bf16 GEMM rate measured on this machine, fp8 taken as twice bf16 (the
+    the bf16 GEMM rate measured on these GPUs, fp8 taken as twice bf16 (the
     nominal ratio of the dense tensor rates)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
