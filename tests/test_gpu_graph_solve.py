@@ -92,3 +92,42 @@ def test_solve_time_limit(pkg):
         r1 = s.solve(130, chunk=40)
         assert r1["steps"] == 130 and len(r1["trace_best_cost"]) == 5
         assert s.best()[1].min() >= 1
+
+
+def test_captured_step_with_dense_evaluation_replays_the_same_work(pkg):
+    """The benchmark times a step captured into a CUDA graph from the library
+    calls (step, then the tensor-core evaluation of the new x).  Replaying it
+    K times leaves exactly the state and costs of K plain calls."""
+    import torch
+    cnf = uniform_ksat(2000, 8600, 3, seed=19)
+    B, K = 64, 12
+    with pkg.Solver.from_cnf(cnf, restarts=B, lr=1e-2) as a, pkg.Solver.from_cnf(cnf, restarts=B, lr=1e-2) as b:
+        ca = torch.empty(B, dtype=torch.int64, device="cuda")
+        cb = torch.empty(B, dtype=torch.int64, device="cuda")
+
+        def step(s, out):
+            s.step_async(1, final_eval=False)
+            s.evaluate_x("dense", out=out)
+
+        for _ in range(2):  # warm-up (first use of the dense backend allocates)
+            step(a, ca)
+            step(b, cb)
+        torch.cuda.synchronize()
+        main = torch.cuda.current_stream()
+        cap = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        b.set_stream(cap)
+        try:
+            with torch.cuda.graph(g, stream=cap):
+                step(b, cb)
+        finally:
+            b.set_stream(main)
+        # capturing records the step without running it: both are at 2 steps
+        for _ in range(K):
+            step(a, ca)
+        for _ in range(K):
+            g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(ca.cpu().numpy(), cb.cpu().numpy())
+        assert np.array_equal(a.x().view(np.uint32), b.x().view(np.uint32))
+        assert np.array_equal(a.best()[1], b.best()[1])
