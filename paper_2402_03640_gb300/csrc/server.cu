@@ -82,6 +82,8 @@ struct SrvDone {
 
 enum { ST_QUEUED = 0, ST_RUNNING = 1, ST_DONE = 2, ST_FAILED = 3 };
 
+constexpr double kAdmitSliceMs = 4.0;  // host admission time between rounds while slots run
+
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
@@ -404,8 +406,13 @@ void worker_main(msat_server *S) {
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
+            // admission builds the instance on the host; while slots are
+            // running it takes short slices, so queued rounds keep the GPU
+            // busy and a burst of requests does not stall the running ones
+            const Clock::time_point t_adm = Clock::now();
             while (!S->queue.empty() && (int)S->slots.size() < S->cfg.max_slots &&
                    S->in_use + S->queue.front().est <= S->cfg.hbm_budget) {
+                if (!S->slots.empty() && ms_between(t_adm, Clock::now()) > kAdmitSliceMs) break;
                 SrvRequest req = std::move(S->queue.front());
                 S->queue.pop_front();
                 S->state[req.ticket] = ST_RUNNING;
