@@ -416,7 +416,14 @@ typedef struct {
     int32_t max_slots;  /* instances stepped together (0 = 256)           */
     int32_t restarts;   /* B of every instance (power of two, <= 1024)    */
     int32_t chunk;      /* steps per scheduling round (0 = 50)            */
-    int32_t reserved;
+    int32_t batch_mlits; /* cap on the work of one step of the batch, in
+                            millions of literal evaluations (nnz x restarts
+                            summed over the instances stepped together and
+                            those being admitted); a request waits while it
+                            would pass the cap, unless nothing else runs.
+                            Past the point where the batch fills the GPU,
+                            more instances only slow every one of them
+                            (0 = 128, < 0 = no cap)                       */
     double lr, beta1, beta2, eps; /* Adam settings of every instance      */
 } msat_server_config;
 

@@ -2,19 +2,22 @@
 //
 // A scheduler thread owns the device work.  Requests wait in a FIFO queue;
 // the oldest is admitted when a slot is free and its estimated device
-// memory fits the budget.  Admission builds an ordinary context with
-// stream-ordered allocations on an admission stream (so it never stalls the
-// compute stream).  All admitted instances advance together: one iteration
-// of Algorithm 1 for the whole slot table is three batched kernels (clause
-// pass, heavy and light variable passes) captured once into a CUDA graph,
-// replayed `chunk` times per round; the table and the graph are rebuilt
-// only when the slot set changes.  An instance that has taken its steps is
-// evaluated once more, its best costs and assignment are copied to pinned
-// host memory behind an event, and its memory is released in stream order
-// once the copy has landed; the freed budget admits queued requests.
+// memory fits the budget.  Admission reserves the slot and the bytes and
+// hands the request to a pool of builder threads: each builds an ordinary
+// context (the host-side CSR work and its upload) with stream-ordered
+// allocations on a stream of its own, so building never stalls the compute
+// stream and a burst of requests is built in parallel.  All placed
+// instances advance together: one iteration of Algorithm 1 for the whole
+// slot table is three batched kernels (clause pass, heavy and light
+// variable passes) captured once into a CUDA graph, replayed `chunk` times
+// per round; the table and the graph are rebuilt only when the slot set
+// changes.  An instance that has taken its steps is evaluated once more,
+// its best costs and assignment are copied to pinned host memory behind an
+// event, and its memory is released in stream order once the copy has
+// landed; the freed budget admits queued requests.
 // An instance small enough for the single-CTA kernel (state in shared
 // memory) skips the slot table: it takes all its steps in one launch on one
-// of several side streams as soon as it is admitted and retires the same
+// of several side streams as soon as it is built and retires the same
 // way, so it is not held back by the large instances of the batch.
 //
 // Instances share no device state, so each result is bit for bit what the
@@ -54,6 +57,7 @@ struct SrvRequest {
     uint64_t seed = 1;
     Clock::time_point t_submit;
     size_t est = 0;
+    int64_t work = 0;  // literal evaluations of one step: nnz x restarts
 };
 
 struct SrvSlot {
@@ -62,6 +66,15 @@ struct SrvSlot {
     int32_t remaining = 0, steps = 0;
     Clock::time_point t_submit, t_admit;
     size_t bytes = 0;
+    int64_t work = 0;
+};
+
+// A request whose context a builder has made (ctx NULL: creation failed
+// and the request is already finished as failed).
+struct SrvBuilt {
+    SrvRequest req;
+    msat_ctx *ctx = nullptr;
+    Clock::time_point t_admit;
 };
 
 struct SrvFinishing {
@@ -82,8 +95,6 @@ struct SrvDone {
 
 enum { ST_QUEUED = 0, ST_RUNNING = 1, ST_DONE = 2, ST_FAILED = 3 };
 
-constexpr double kAdmitSliceMs = 4.0;  // host admission time between rounds while slots run
-
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
@@ -93,16 +104,23 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 struct msat_server {
     msat_server_config cfg{};
     int device = 0;
-    cudaStream_t compute = nullptr, admit = nullptr;
+    cudaStream_t compute = nullptr;
     // small requests run apart from the slot table, round robin over these
     static constexpr int kSmallStreams = 16;
     cudaStream_t small_st[kSmallStreams] = {};
     int small_next = 0;
     std::thread worker;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_build;
     bool stop = false;
     std::deque<SrvRequest> queue;
+    // builder pool: requests handed over for context creation, and the
+    // contexts made, waiting for the scheduler to place them
+    std::vector<std::thread> builders;
+    std::vector<cudaStream_t> build_st;
+    std::deque<SrvRequest> build_q;
+    std::deque<SrvBuilt> ready;
+    bool stop_build = false;
     std::unordered_map<uint64_t, int> state;
     std::unordered_map<uint64_t, SrvDone> done;
     uint64_t next_ticket = 1;
@@ -111,7 +129,10 @@ struct msat_server {
     // scheduler-owned
     std::vector<SrvSlot> slots;
     std::vector<SrvFinishing> finishing;
-    size_t in_use = 0;
+    size_t in_use = 0;   // placed and finishing instances, plus reservations of those being built
+    int building = 0;    // requests handed to the builders and not yet placed
+    int64_t work = 0;    // step work of the slot table plus that of the requests being built
+    int64_t work_cap = 0;
     SlotDesc *d_slots = nullptr;
     int *d_starts = nullptr;          // fwd[max+1], heavy[max+1], light[max+1]
     SlotDesc *h_slots[2] = {nullptr, nullptr};
@@ -197,7 +218,7 @@ cudaError_t start_retire(msat_server *S, const SrvSlot &sl) {
     return e;
 }
 
-void admit(msat_server *S, SrvRequest &req) {
+msat_config request_config(const msat_server *S, const SrvRequest &req) {
     msat_config cfg;
     msat_config_default(&cfg);
     cfg.lr = S->cfg.lr;
@@ -209,20 +230,61 @@ void admit(msat_server *S, SrvRequest &req) {
     cfg.f_mode = MSAT_F_STORE;  // batched kernels use the stored-f path
     cfg.fwd_vw = S->fwd_vw;
     cfg.stage_vw = S->stage_vw;
-    msat_ctx *c = nullptr;
-    const int rc = ctx_create(&c, req.n, req.m, req.off.data(), req.lits.data(),
-                              req.w.empty() ? nullptr : req.w.data(), &cfg, S->admit, true);
-    if (rc) {
-        finish_failed(S, req.ticket, rc, req.t_submit);
-        return;
+    return cfg;
+}
+
+// Builder thread k: create the context of each handed-over request on
+// stream k (the creation ends with that stream synchronised, so the
+// context is ready for any stream), then pass it back to the scheduler.
+void builder_main(msat_server *S, int k) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        SrvRequest req;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_build.wait(lk, [&] { return S->stop_build || !S->build_q.empty(); });
+            if (S->build_q.empty()) return;
+            req = std::move(S->build_q.front());
+            S->build_q.pop_front();
+        }
+        const msat_config cfg = request_config(S, req);
+        msat_ctx *c = nullptr;
+        const int rc = ctx_create(&c, req.n, req.m, req.off.data(), req.lits.data(),
+                                  req.w.empty() ? nullptr : req.w.data(), &cfg, S->build_st[(size_t)k], true);
+        if (rc) finish_failed(S, req.ticket, rc, req.t_submit);
+        SrvBuilt b;
+        b.ctx = rc ? nullptr : c;
+        b.t_admit = Clock::now();
+        b.req.ticket = req.ticket;
+        b.req.steps = req.steps;
+        b.req.t_submit = req.t_submit;
+        b.req.est = req.est;
+        b.req.work = req.work;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->ready.push_back(std::move(b));
+        }
+        S->cv_work.notify_one();
     }
+}
+
+// Scheduler side of admission: swap the request's reservation for the
+// context's real bytes and start it, either directly (small instances) or
+// as a new slot of the batched table.
+void place(msat_server *S, SrvBuilt &b) {
+    S->building--;
+    S->in_use -= b.req.est;
+    S->work -= b.req.work;
+    msat_ctx *c = b.ctx;
+    if (!c) return;  // creation failed; the request is finished already
+    const SrvRequest &req = b.req;
     SrvSlot sl;
     sl.ticket = req.ticket;
     sl.ctx = c;
     sl.remaining = req.steps;
     sl.steps = req.steps;
     sl.t_submit = req.t_submit;
-    sl.t_admit = Clock::now();
+    sl.t_admit = b.t_admit;
     sl.bytes = (size_t)c->device_bytes;
     S->in_use += sl.bytes;
     if (small_fits(c->I, c->max_deg)) {
@@ -243,6 +305,8 @@ void admit(msat_server *S, SrvRequest &req) {
         return;
     }
     c->stream = S->compute;  // every later kernel of this instance runs on the compute stream
+    sl.work = req.work;
+    S->work += sl.work;
     S->slots.push_back(sl);
     S->dirty = true;
 }
@@ -339,6 +403,7 @@ int run_round_body(msat_server *S) {
         }
         const cudaError_t e = start_retire(S, sl);
         if (e) return cuda_fail(e, "msat server: result copy");
+        S->work -= sl.work;
         S->dirty = true;
     }
     S->slots.swap(keep);
@@ -401,50 +466,82 @@ void reap(msat_server *S, bool block) {
     S->finishing.swap(pending);
 }
 
+// A slot is free, the oldest request's estimate fits the budget and its
+// step work fits the batch cap (or nothing else is running or being
+// built); the caller holds the lock.
+bool can_admit(const msat_server *S) {
+    if (S->queue.empty()) return false;
+    const SrvRequest &r = S->queue.front();
+    const bool alone = S->slots.empty() && S->building == 0;
+    return (int)S->slots.size() + S->building < S->cfg.max_slots &&
+           S->in_use + r.est <= S->cfg.hbm_budget &&
+           (S->work_cap <= 0 || alone || S->work + r.work <= S->work_cap);
+}
+
 void worker_main(msat_server *S) {
     cudaSetDevice(S->device);
+    std::deque<SrvBuilt> got;
     for (;;) {
+        bool block_reap = false;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // admission builds the instance on the host; while slots are
-            // running it takes short slices, so queued rounds keep the GPU
-            // busy and a burst of requests does not stall the running ones
-            const Clock::time_point t_adm = Clock::now();
-            while (!S->queue.empty() && (int)S->slots.size() < S->cfg.max_slots &&
-                   S->in_use + S->queue.front().est <= S->cfg.hbm_budget) {
-                if (!S->slots.empty() && ms_between(t_adm, Clock::now()) > kAdmitSliceMs) break;
-                SrvRequest req = std::move(S->queue.front());
-                S->queue.pop_front();
+            // admission in FIFO order: reserve a slot and the estimated
+            // bytes, and hand the request to the builders
+            bool handed = false;
+            while (can_admit(S)) {
+                SrvRequest &req = S->queue.front();
                 S->state[req.ticket] = ST_RUNNING;
-                lk.unlock();
-                admit(S, req);
-                lk.lock();
+                S->in_use += req.est;
+                S->work += req.work;
+                S->building++;
+                S->build_q.push_back(std::move(req));
+                S->queue.pop_front();
+                handed = true;
             }
+            if (handed) S->cv_build.notify_all();
+            got.swap(S->ready);
+            const bool idle = got.empty() && S->slots.empty();
+            if (idle && S->finishing.empty()) {
+                if (S->stop && S->queue.empty() && S->building == 0) break;
+                S->cv_work.wait(lk, [&] {
+                    return (S->stop && S->queue.empty() && S->building == 0) || !S->ready.empty() ||
+                           can_admit(S);
+                });
+                continue;
+            }
+            if (idle) {
+                // only results in flight: wait for them, unless contexts are
+                // still being built (then poll, so a built one is placed soon)
+                if (S->building > 0)
+                    S->cv_work.wait_for(lk, std::chrono::microseconds(200), [&] { return !S->ready.empty(); });
+                else
+                    block_reap = true;
+            }
+        }
+        for (SrvBuilt &b : got) place(S, b);
+        got.clear();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
             S->st.running = (int32_t)S->slots.size();
             S->st.peak_running = std::max(S->st.peak_running, S->st.running);
             S->st.queued = (int32_t)S->queue.size();
             S->st.hbm_in_use = (int64_t)S->in_use;
-            if (S->slots.empty() && S->finishing.empty()) {
-                if (S->stop && S->queue.empty()) break;
-                S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
-                continue;
-            }
         }
         if (!S->slots.empty()) {
             const int rc = run_round(S);
             if (rc) {
                 // a CUDA failure in the shared loop fails every running request
-                const std::string msg = msat_last_error();
                 for (SrvSlot &sl : S->slots) {
                     finish_failed(S, sl.ticket, rc, sl.t_submit);
                     ctx_destroy_async(sl.ctx);
                     S->in_use -= sl.bytes;
+                    S->work -= sl.work;
                 }
                 S->slots.clear();
                 S->dirty = true;
             }
         }
-        reap(S, S->slots.empty());
+        reap(S, block_reap);
     }
 }
 
@@ -456,6 +553,7 @@ extern "C" int msat_server_config_default(msat_server_config *cfg) {
     cfg->max_slots = 256;
     cfg->restarts = 8;
     cfg->chunk = 50;
+    cfg->batch_mlits = 128;
     cfg->lr = 1e-4;
     cfg->beta1 = 0.9;
     cfg->beta2 = 0.999;
@@ -470,6 +568,7 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     if (cfg_in) cfg = *cfg_in; else msat_server_config_default(&cfg);
     if (cfg.max_slots <= 0) cfg.max_slots = 256;
     if (cfg.chunk <= 0) cfg.chunk = 50;
+    if (cfg.batch_mlits == 0) cfg.batch_mlits = 128;
     const int B = cfg.restarts;
     if (B < 1 || B > 1024 || (B & (B - 1)))
         return fail(MSAT_EINVAL, "msat_server_create: restarts must be a power of two in [1, 1024]");
@@ -485,12 +584,18 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
         cfg.hbm_budget = fr / 2;
     }
     S->cfg = cfg;
+    S->work_cap = cfg.batch_mlits > 0 ? (int64_t)cfg.batch_mlits * 1000000 : 0;
     S->fwd_vw = auto_fwd_vw(B);
     S->stage_vw = auto_stage_vw(B);
     S->task_cap = std::max(kTaskCap, B / S->stage_vw);
     const int M = cfg.max_slots + 1;
+    // builders: half the host's hardware threads, 1 to 8
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int n_build = (int)std::min(8u, std::max(1u, hc / 2));
+    S->build_st.assign((size_t)n_build, nullptr);
     cudaError_t e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
-    if (!e) e = cudaStreamCreateWithFlags(&S->admit, cudaStreamNonBlocking);
+    for (int k = 0; k < n_build && !e; ++k)
+        e = cudaStreamCreateWithFlags(&S->build_st[(size_t)k], cudaStreamNonBlocking);
     for (int k = 0; k < msat_server::kSmallStreams && !e; ++k)
         e = cudaStreamCreateWithFlags(&S->small_st[k], cudaStreamNonBlocking);
     if (!e) e = cudaMalloc(&S->d_slots, sizeof(SlotDesc) * (size_t)cfg.max_slots);
@@ -516,6 +621,7 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
         return rc;
     }
     S->st.hbm_budget = (int64_t)cfg.hbm_budget;
+    for (int k = 0; k < n_build; ++k) S->builders.emplace_back(builder_main, S, k);
     S->worker = std::thread(worker_main, S);
     *out = S;
     return MSAT_OK;
@@ -528,7 +634,14 @@ extern "C" void msat_server_destroy(msat_server *S) {
         S->stop = true;
     }
     S->cv_work.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    if (S->worker.joinable()) S->worker.join();  // returns once nothing is queued or being built
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop_build = true;
+    }
+    S->cv_build.notify_all();
+    for (std::thread &t : S->builders)
+        if (t.joinable()) t.join();
     if (S->compute) cudaStreamSynchronize(S->compute);
     for (cudaStream_t st : S->small_st)
         if (st) cudaStreamSynchronize(st);
@@ -543,7 +656,8 @@ extern "C" void msat_server_destroy(msat_server *S) {
     }
     for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
     if (S->compute) cudaStreamDestroy(S->compute);
-    if (S->admit) cudaStreamDestroy(S->admit);
+    for (cudaStream_t st : S->build_st)
+        if (st) cudaStreamDestroy(st);
     for (cudaStream_t st : S->small_st)
         if (st) cudaStreamDestroy(st);
     delete S;
@@ -575,6 +689,7 @@ extern "C" int msat_submit(msat_server *S, const msat_request *req, uint64_t *ti
     r.lits.assign(req->lits, req->lits + nnz);
     if (req->weights) r.w.assign(req->weights, req->weights + m);
     r.est = estimate_bytes(r.n, m, nnz, req->weights != nullptr, S->cfg.restarts);
+    r.work = nnz * (int64_t)S->cfg.restarts;
     if (r.est > S->cfg.hbm_budget)
         return fail(MSAT_EBUDGET, "msat_submit: the instance needs about " + std::to_string(r.est) +
                                       " device bytes, above the server budget of " +

@@ -63,7 +63,7 @@ class msat_info(ctypes.Structure):
 
 class msat_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
-                ("restarts", ctypes.c_int32), ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("chunk", ctypes.c_int32), ("batch_mlits", ctypes.c_int32),
                 ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double)]
 

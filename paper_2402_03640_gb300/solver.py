@@ -275,7 +275,8 @@ class Server:
     at any time, poll or wait for their results."""
 
     def __init__(self, restarts: int = 8, hbm_budget: int = 0, max_slots: int = 0, chunk: int = 0,
-                 lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+                 lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                 batch_mlits: int = 0):
         lib = native.load()
         self._lib = lib
         cfg = native.msat_server_config()
@@ -286,6 +287,7 @@ class Server:
             cfg.max_slots = int(max_slots)
         if chunk:
             cfg.chunk = int(chunk)
+        cfg.batch_mlits = int(batch_mlits)
         cfg.lr, cfg.beta1, cfg.beta2, cfg.eps = lr, beta1, beta2, eps
         self.B = int(restarts)
         self._srv = ctypes.c_void_p()

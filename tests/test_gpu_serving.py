@@ -82,6 +82,32 @@ def test_budget_limits_concurrency(pkg):
     assert st["hbm_in_use"] <= 6 << 20
 
 
+def test_work_cap_limits_batch(pkg):
+    """batch_mlits bounds the step work of the instances stepped together:
+    each request below does 2000 x 8600 x 3 x 8 = 206,400 literal evaluations
+    a step, so a cap of 10^6 holds at most 4 of them; a request above the cap
+    still runs once nothing else does.  Results stay those of the request
+    alone."""
+    cnfs = [uniform_ksat(2000, 8600, 3, seed=s) for s in range(8)]
+    big = uniform_ksat(20000, 86000, 3, seed=9)  # 2,064,000 a step
+    with pkg.Server(restarts=8, chunk=10, batch_mlits=1) as srv:
+        tickets = [srv.submit(c, 40, seed_x=s) for s, c in enumerate(cnfs)]
+        tb = srv.submit(big, 20, seed_x=3)
+        res = [srv.wait(t, 300) for t in tickets]
+        rb = srv.wait(tb, 300)
+        st = srv.stats()
+    assert all(r["status"] == 0 for r in res) and rb["status"] == 0
+    assert 1 <= st["peak_running"] <= 4
+    for s in (0, 7):
+        best, _ = _alone(pkg, cnfs[s], 8, 40, s, 1e-4)
+        assert np.array_equal(res[s]["best_costs"], best)
+    best, _ = _alone(pkg, big, 8, 20, 3, 1e-4)
+    assert np.array_equal(rb["best_costs"], best)
+    with pkg.Server(restarts=8, chunk=10, batch_mlits=-1) as srv:  # no cap
+        r = srv.wait(srv.submit(cnfs[1], 40, seed_x=1), 300)
+    assert np.array_equal(r["best_costs"], res[1]["best_costs"])
+
+
 def test_over_budget_and_malformed_requests(pkg):
     from paper_2402_03640_gb300 import MsatError, native
     with pkg.Server(restarts=8, hbm_budget=1 << 20) as srv:
