@@ -226,9 +226,10 @@ int msat_autotune(int32_t n_vars, int64_t n_clauses, const int64_t *clause_off,
  *   cost_out    device int64[nb]: sum of w_j over clauses with no true literal
  *   backend     MSAT_BACKEND_SPARSE or MSAT_BACKEND_DENSE
  * Asynchronous on the context stream; the result is exact for both
- * backends.  The dense backend multiplies the clause matrix W^T (e4m3,
- * m x n, built on its first use: m_pad * n_pad bytes, rejected above
- * 64 GiB) by the batch on the tensor cores; it needs weights below 2^25.
+ * backends.  The dense backend multiplies the clause matrix W^T (e2m1,
+ * m x n, packed two codes a byte, built on its first use: m_pad * n_pad / 2
+ * bytes, rejected above 64 GiB) by the batch on the tensor cores; it needs
+ * weights below 2^25.
  */
 int msat_evaluate(msat_ctx *ctx, const int8_t *assign_pm1, int32_t nb, int64_t *cost_out,
                   int32_t backend);

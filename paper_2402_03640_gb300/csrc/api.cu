@@ -653,8 +653,8 @@ extern "C" int msat_profile_read(msat_ctx *c, msat_profile *out, int reset) {
     return MSAT_OK;
 }
 
-// First use of the dense backend: the e4m3 clause matrix W^T [m_pad][n_pad]
-// (zero padding), per-clause targets -len_j (NaN for padding rows and for
+// First use of the dense backend: the clause matrix W^T [m_pad][n_pad] in
+// packed e2m1 (two codes a byte, zero padding), per-clause targets -len_j (NaN for padding rows and for
 // clauses holding some x and not x, which are never unsat), 32-bit weights
 // and the TMA descriptor of W^T.
 static int dense_setup(msat_ctx *c) {
@@ -665,12 +665,12 @@ static int dense_setup(msat_ctx *c) {
     DenseDev &d = c->dense;
     d.m_pad = (int)std::max<int64_t>(128, (c->m + 127) / 128 * 128);
     d.n_pad = (c->n + 127) / 128 * 128;
-    const double bytes = (double)d.m_pad * (double)d.n_pad;
+    const double bytes = (double)d.m_pad * (double)d.n_pad / 2;
     if (bytes > 64.0 * (1LL << 30))
         return fail(MSAT_EINVAL, "msat_evaluate: the dense clause matrix would take " +
                                      std::to_string((long long)(bytes / (1 << 20))) + " MiB (limit 64 GiB)");
     int rc;
-    if ((rc = dalloc_t(c, &d.Wt, (size_t)d.m_pad * d.n_pad))) return rc;
+    if ((rc = dalloc_t(c, &d.Wt, (size_t)d.m_pad * d.n_pad / 2))) return rc;
     if ((rc = dalloc_t(c, &d.target, (size_t)d.m_pad))) return rc;
     if ((rc = dalloc_t(c, &d.wgt, (size_t)d.m_pad))) return rc;
     if ((rc = dalloc_t(c, &d.errflag, 1))) return rc;
@@ -681,7 +681,7 @@ static int dense_setup(msat_ctx *c) {
         w32[(size_t)j] = c->wts.empty() ? 1u : (uint32_t)c->wts[(size_t)j];
     }
     cudaStream_t st = c->stream;
-    MSAT_CUDA_TRY(cudaMemsetAsync(d.Wt, 0, (size_t)d.m_pad * d.n_pad, st));
+    MSAT_CUDA_TRY(cudaMemsetAsync(d.Wt, 0, (size_t)d.m_pad * d.n_pad / 2, st));
     MSAT_CUDA_TRY(cudaMemsetAsync(d.errflag, 0, sizeof(unsigned), st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(d.target, tgt.data(), sizeof(float) * tgt.size(), cudaMemcpyHostToDevice, st));
     MSAT_CUDA_TRY(cudaMemcpyAsync(d.wgt, w32.data(), sizeof(uint32_t) * w32.size(), cudaMemcpyHostToDevice, st));
@@ -733,7 +733,7 @@ static int dense_eval(msat_ctx *c, const int8_t *a, const float *x, int32_t nb, 
     int rc = dense_setup(c);
     if (rc) return rc;
     const int rows = dense_rows(nb), ntile = dense_tile_n(nb);
-    const size_t need = (size_t)rows * c->dense.n_pad;
+    const size_t need = (size_t)rows * c->dense.n_pad / 2;  // packed 4-bit codes
     if (need > c->dense.xt_bytes) {
         if (c->dense.Xt) {
             cudaStreamSynchronize(c->stream);

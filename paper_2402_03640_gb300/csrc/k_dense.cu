@@ -7,8 +7,13 @@
 // [S_jb = -len_j].
 //
 // tcgen05.mma .kind::i8 is not available on sm_103a, so both operands are
-// e4m3 (0, +1, -1 are exact) with fp32 accumulation, which is exact here:
-// every partial sum is an integer of magnitude <= n < 2^24.
+// e2m1 (0, +1, -1 are exact) with fp32 accumulation, which is exact here:
+// every partial sum is an integer of magnitude <= n < 2^24.  In global
+// memory the operands are packed, two 4-bit codes a byte; the TMA loads
+// (tensor maps of type 16U4_ALIGN16B) expand them into the padded layout
+// .kind::f8f6f4 reads (16 codes in the first 8 bytes of each 16-byte
+// chunk), so shared memory holds one byte per element as with 8-bit types
+// while HBM, L2 and the path into each SM carry half the bytes.
 //
 // Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 128
 // variables per stage.  Warp 0 (one lane) loads A and B tiles with TMA into
@@ -33,13 +38,14 @@ namespace msat {
 namespace {
 
 constexpr int kTM = 128;            // clauses per tile (MMA M)
-constexpr int kTK = 128;            // variables per stage (128 bytes of e4m3)
+constexpr int kTK = 128;            // variables per stage (128 bytes a row in shared memory)
 constexpr int kStages = 4;
 constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
 constexpr long long kSpin = 1LL << 26;
-constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
+// e2m1 codes (sign, 2 exponent bits with bias 1, 1 mantissa bit)
+constexpr uint8_t kE2M1One = 0x2, kE2M1MinusOne = 0xA;
 
 struct DenseHeader {
     unsigned long long full[kStages];
@@ -117,16 +123,16 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor of kind::f8f6f4: D fp32, A and B e4m3, both
+// Instruction descriptor of kind::f8f6f4: D fp32, A and B e2m1, both
 // K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_e4m3(int n) {
+__device__ __forceinline__ uint32_t idesc_e2m1(int n) {
     return (1u << 4)                      // D format fp32
-           | (0u << 7) | (0u << 10)       // A, B format e4m3
+           | (5u << 7) | (5u << 10)       // A, B format e2m1
            | ((uint32_t)(n >> 3) << 17)   // N / 8
            | ((uint32_t)(kTM >> 4) << 24);  // M / 16
 }
 
-__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f8f6f4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -211,7 +217,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
                 }
             }
             uint8_t *sa = stages + (size_t)s * stage_bytes;
-            mbar_expect_tx(&H->full[s], stage_bytes);
+            // the transaction count of a packed-type load is the bytes it
+            // reads (two codes a byte), half what it writes to shared memory
+            mbar_expect_tx(&H->full[s], stage_bytes / 2);
             tma_load_2d(sa, &tmA, kt * kTK, m0, &H->full[s]);
             tma_load_2d(sa + a_bytes, &tmB, kt * kTK, n0, &H->full[s]);
             issued = kt + 1;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             if (!mbar_wait(&H->full[kt % kStages], (uint32_t)((kt / kStages) & 1), kSpin)) atomicOr(errflag, 2u);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = idesc_e4m3(ntile);
+        const uint32_t idesc = idesc_e2m1(ntile);
         for (int kt = 0; kt < kt_count; ++kt) {
             const int s = kt % kStages;
             if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((kt / kStages) & 1), kSpin)) {
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             const uint64_t bdesc = smem_desc_sw128(sa + a_bytes);
 #pragma unroll
             for (int kk = 0; kk < kTK / 32; ++kk)  // K = 32 bytes per MMA: +2 in the 16-byte address field
-                mma_e4m3(tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt | kk) != 0);
+                mma_f8f6f4(tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt | kk) != 0);
             mma_commit(&H->empty[s]);
         }
         mma_commit(&H->done);  // arrives once every MMA issued above has completed
@@ -288,10 +296,14 @@ __global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
     }
 }
 
-// W^T in e4m3: row j holds +1 / -1 at the columns of the clause's literals
-// (the buffer was zeroed).  A clause with x and not x writes both; its target
-// is NaN, so it never counts.
+// W^T in packed e2m1: row j (n_pad / 2 bytes) holds +1 / -1 at the columns
+// of the clause's literals, variable i in the low (i even) or high nibble
+// of byte i / 2 (the buffer was zeroed).  One thread owns a row, so the
+// read-modify-write of a byte shared by two literals is race-free.  A
+// clause with x and not x writes both into the same nibble; its target is
+// NaN, so it never counts.
 __global__ void k_dense_fill(DevInst I, uint8_t *__restrict__ Wt, int n_pad) {
+    const long long row_bytes = n_pad / 2;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < I.m;
          j += (long long)gridDim.x * blockDim.x) {
         int beg, end;
@@ -302,52 +314,52 @@ __global__ void k_dense_fill(DevInst I, uint8_t *__restrict__ Wt, int n_pad) {
             beg = I.coff[j];
             end = I.coff[j + 1];
         }
+        uint8_t *row = Wt + j * row_bytes;
         for (int p = beg; p < end; ++p) {
             const int L = I.lit[p];
-            Wt[j * n_pad + (L >> 1)] = (L & 1) ? kE4M3MinusOne : kE4M3One;
+            const int v = L >> 1, sh = (v & 1) * 4;
+            const uint8_t code = (L & 1) ? kE2M1MinusOne : kE2M1One;
+            row[v >> 1] = (uint8_t)((row[v >> 1] & ~(0xF << sh)) | (code << sh));
         }
     }
 }
 
-// X^T in e4m3 from the caller's int8 [n][nb] batch (> 0 is true): rows =
-// assignments, n_pad columns, zero padding; 32 x 32 tiles through shared
-// memory so both sides are coalesced.
-__global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uint8_t *__restrict__ Xt,
-                                int n_pad, int rows) {
-    __shared__ uint8_t tile[32][33];
-    const int v0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+// X^T in packed e2m1 (rows = assignments, n_pad / 2 bytes each, zero
+// padding) from a batch stored [n][nb]: a block transposes 64 variables x
+// 32 assignments through shared memory, reading along the batch and
+// writing 32 bytes (64 codes) of each assignment's row.
+template <typename T>
+__device__ __forceinline__ void pack_transpose(const T *__restrict__ src, int n, int nb, uint8_t *__restrict__ Xt,
+                                               int n_pad, int rows) {
+    __shared__ uint8_t tile[64][33];
+    const int v0 = blockIdx.x * 64, b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 64; r += blockDim.y) {
         const int v = v0 + r, b = b0 + threadIdx.x;
         uint8_t e = 0;
-        if (v < n && b < nb) e = a[(long long)v * nb + b] > 0 ? kE4M3One : kE4M3MinusOne;
+        if (v < n && b < nb) e = src[(long long)v * nb + b] > (T)0 ? kE2M1One : kE2M1MinusOne;
         tile[r][threadIdx.x] = e;
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int b = b0 + r, v = v0 + threadIdx.x;
-        if (b < rows && v < n_pad) Xt[(long long)b * n_pad + v] = tile[threadIdx.x][r];
+        const int b = b0 + r, t = threadIdx.x;
+        if (b < rows)
+            Xt[(long long)b * (n_pad / 2) + v0 / 2 + t] = (uint8_t)(tile[2 * t][r] | (tile[2 * t + 1][r] << 4));
     }
+}
+
+// From the caller's int8 [n][nb] batch (> 0 is true).
+__global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uint8_t *__restrict__ Xt,
+                                int n_pad, int rows) {
+    pack_transpose<int8_t>(a, n, nb, Xt, n_pad, rows);
 }
 
 // The same operand straight from the relaxed x (float [n][nb]): x > 0 reads
 // as +1, otherwise -1 -- the rounding of Sec. 4 -- without the int8 copy.
 __global__ void k_dense_convert_x(const float *__restrict__ x, int n, int nb, uint8_t *__restrict__ Xt,
                                   int n_pad, int rows, long long *__restrict__ cost) {
-    __shared__ uint8_t tile[32][33];
-    const int v0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
     if (blockIdx.x == 0 && blockIdx.y == 0)  // the GEMM that follows in stream order adds into cost
         for (int b = threadIdx.y * 32 + threadIdx.x; b < nb; b += 32 * blockDim.y) cost[b] = 0;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int v = v0 + r, b = b0 + threadIdx.x;
-        uint8_t e = 0;
-        if (v < n && b < nb) e = x[(long long)v * nb + b] > 0.0f ? kE4M3One : kE4M3MinusOne;
-        tile[r][threadIdx.x] = e;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int b = b0 + r, v = v0 + threadIdx.x;
-        if (b < rows && v < n_pad) Xt[(long long)b * n_pad + v] = tile[threadIdx.x][r];
-    }
+    pack_transpose<float>(x, n, nb, Xt, n_pad, rows);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -365,15 +377,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2D uint8 tensor [rows][cols] (cols contiguous), box 128 x box_rows, 128B swizzle.
+// 2D tensor of packed 4-bit codes [rows][cols] (cols contiguous, cols / 2
+// bytes a row; cols a multiple of 128), box 128 x box_rows, expanded into
+// the padded shared-memory layout with 128B swizzle.
 int encode_2d(CUtensorMap *map, void *base, long long cols, long long rows, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return fail(MSAT_ECUDA, "dense backend: cuTensorMapEncodeTiled is not available");
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)(cols / 2)};
     const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B, 2, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
@@ -415,7 +429,7 @@ cudaError_t launch_dense_fill(const DevInst &I, uint8_t *Wt, int n_pad, cudaStre
 
 cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int nb, long long *cost,
                                  cudaStream_t st) {
-    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
+    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 64), (unsigned)((d.tmB_rows + 31) / 32));
     k_dense_convert<<<cg, cb, 0, st>>>(a, n, nb, d.Xt, d.n_pad, d.tmB_rows);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
@@ -424,7 +438,7 @@ cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int 
 
 cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
                                    cudaStream_t st) {
-    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 32), (unsigned)((d.tmB_rows + 31) / 32));
+    dim3 cb(32, 8), cg((unsigned)(d.n_pad / 64), (unsigned)((d.tmB_rows + 31) / 32));
     k_dense_convert_x<<<cg, cb, 0, st>>>(x, n, nb, d.Xt, d.n_pad, d.tmB_rows, cost);
     return cudaGetLastError();
 }

@@ -95,9 +95,10 @@ struct DevState {
                            // nullptr: the variable pass recomputes f from the unsat bits
 };
 
-// Dense tensor-core evaluation (k_dense.cu): e4m3 clause matrix W^T
-// [m_pad][n_pad], per-row target -len_j (NaN: never unsat), 32-bit weights,
-// the e4m3 assignment batch X^T [rows][n_pad] and their TMA descriptors.
+// Dense tensor-core evaluation (k_dense.cu): clause matrix W^T
+// [m_pad][n_pad] in packed e2m1 (n_pad / 2 bytes a row), per-row target
+// -len_j (NaN: never unsat), 32-bit weights, the packed e2m1 assignment
+// batch X^T [rows][n_pad] and their TMA descriptors.
 struct DenseDev {
     uint8_t *Wt = nullptr;
     float *target = nullptr;

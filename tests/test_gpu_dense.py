@@ -1,4 +1,4 @@
-"""Dense tensor-core evaluation (e4m3 W^T times the +-1 batch, exact fp32
+"""Dense tensor-core evaluation (packed e2m1 W^T times the +-1 batch, exact fp32
 accumulation) against the sparse evaluator and the oracle's exact cost:
 bit-exact integers for every assignment."""
 import numpy as np
