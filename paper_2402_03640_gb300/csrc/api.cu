@@ -100,6 +100,14 @@ static void free_all(msat_ctx *c) {
     if (c->dense.Xt) cudaFree(c->dense.Xt);
     c->dense.Xt = nullptr;
     c->dense.xt_bytes = 0;
+    if (c->dense.ptgt) cudaFree(c->dense.ptgt);
+    if (c->dense.pmask) cudaFree(c->dense.pmask);
+    if (c->dense.part_cnt) cudaFree(c->dense.part_cnt);
+    c->dense.ptgt = nullptr;
+    c->dense.pmask = nullptr;
+    c->dense.part_cnt = nullptr;
+    c->dense.ptgt_slots = c->dense.part_cnts = c->dense.pmask_ntile = 0;
+    c->dense.plan_grid = -1;
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
     c->prof_kind.clear();
@@ -689,6 +697,10 @@ static int dense_setup(msat_ctx *c) {
     if (e) return cuda_fail(e, "msat_evaluate: dense matrix fill");
     MSAT_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above are freed on return
     if ((rc = dense_encode_a(d))) return rc;
+    if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        d.sm_count = 0;
+    }
     c->dense_ready = true;
     return MSAT_OK;
 }
@@ -701,6 +713,9 @@ extern "C" int msat_check(msat_ctx *c) {
         MSAT_CUDA_TRY(cudaMemcpy(&flag, c->dense.errflag, sizeof(flag), cudaMemcpyDeviceToHost));
         if (flag) {
             MSAT_CUDA_TRY(cudaMemset(c->dense.errflag, 0, sizeof(unsigned)));
+            // an aborted launch may have left split-tile counts behind
+            if (c->dense.part_cnt)
+                MSAT_CUDA_TRY(cudaMemset(c->dense.part_cnt, 0, sizeof(unsigned) * c->dense.part_cnts));
             return fail(MSAT_ETIMEOUT, "a bounded wait in the dense evaluation kernel gave up (flag " +
                                            std::to_string(flag) + ")");
         }
@@ -753,6 +768,45 @@ static int dense_eval(msat_ctx *c, const int8_t *a, const float *x, int32_t nb, 
     if (c->dense.tmB_rows != rows || c->dense.tmB_ntile != ntile) {
         rc = dense_encode_b(c->dense, rows, ntile);
         if (rc) return rc;
+    }
+    {
+        // split tiles: per-piece targets (built when the plan changes), the
+        // pieces' bit masks and their counters (zeroed once; every launch
+        // leaves them zeroed)
+        DenseDev &d = c->dense;
+        int grid = 0;
+        const DenseSched p = dense_plan(d, ntile, &grid);
+        if (p.tail > 0) {
+            const int slots = p.tail * p.split;
+            if (slots > d.ptgt_slots || p.tail > d.part_cnts || ntile != d.pmask_ntile) {
+                cudaStreamSynchronize(c->stream);
+                if (d.ptgt) cudaFree(d.ptgt);
+                if (d.pmask) cudaFree(d.pmask);
+                if (d.part_cnt) cudaFree(d.part_cnt);
+                d.ptgt = nullptr;
+                d.pmask = nullptr;
+                d.part_cnt = nullptr;
+                d.ptgt_slots = d.part_cnts = d.pmask_ntile = 0;
+                d.plan_grid = -1;
+                cudaError_t e = cudaMalloc(&d.ptgt, sizeof(float) * (size_t)slots * 128);
+                if (!e) e = cudaMalloc(&d.pmask, sizeof(uint32_t) * (size_t)slots * ((ntile + 31) / 32) * 128);
+                if (!e) e = cudaMalloc(&d.part_cnt, sizeof(unsigned) * (size_t)p.tail);
+                if (!e) e = cudaMemsetAsync(d.part_cnt, 0, sizeof(unsigned) * (size_t)p.tail, c->stream);
+                if (e) {
+                    cudaGetLastError();
+                    return fail(MSAT_ENOMEM, "msat_evaluate: dense split-tile buffer allocation failed");
+                }
+                d.ptgt_slots = slots;
+                d.part_cnts = p.tail;
+                d.pmask_ntile = ntile;
+            }
+            if (grid != d.plan_grid || memcmp(&p, &d.plan, sizeof(p)) != 0) {
+                cudaError_t e = launch_dense_piece_targets(c->I, d, p, grid, c->stream);
+                if (e) return cuda_fail(e, "msat_evaluate: dense piece targets");
+                d.plan = p;
+                d.plan_grid = grid;
+            }
+        }
     }
     prof_begin(c, PROF_OTHER);
     cudaError_t e = x ? launch_dense_convert_x(c->dense, x, c->n, nb, (long long *)cost_out, c->stream)

@@ -18,11 +18,23 @@
 // Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 128
 // variables per stage.  Warp 0 (one lane) loads A and B tiles with TMA into
 // a 4-stage ring of 128B-swizzled shared-memory buffers; warp 1 (one lane)
-// issues tcgen05.mma into a TMEM accumulator and releases each stage with
-// tcgen05.commit; warps 2-5 read the accumulator with tcgen05.ld (one TMEM
-// lane quarter each), compare with -len_j and reduce the weighted unsat
-// counts per column.  Every mbarrier wait is bounded: on a timeout the block
-// records an error flag, stops issuing work and still frees its TMEM.
+// issues tcgen05.mma into one of two TMEM accumulators and releases each
+// stage with tcgen05.commit; warps 2-5 read the accumulator with tcgen05.ld
+// (one TMEM lane quarter each), compare with -len_j and reduce the weighted
+// unsat counts per column, while the next segment accumulates into the
+// other buffer.
+//
+// Schedule: with more tiles than SMs, every CTA of a one-per-SM grid takes
+// the same number of whole tiles, and when the leftover tiles would fill at
+// most half a wave they are split instead, each into `split` equal k-step
+// pieces on as many CTAs.  Every term of S_jb is -1, 0 or +1, so S_jb =
+// -len_j exactly when, in every piece, the piece's partial sum equals minus
+// the number of the clause's literals whose variable lies in the piece's
+// k-range.  A piece therefore tests its own partial sums against those
+// per-piece targets, stores one bit per (clause, assignment) and counts
+// itself in; the last piece of a tile to arrive ANDs the other pieces' bits
+// into its own and counts the unsat clauses.  No CTA waits on another.  Every mbarrier wait is bounded: on a timeout the block records
+// an error flag, stops issuing work and still frees its TMEM.
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -40,6 +52,7 @@ namespace {
 constexpr int kTM = 128;            // clauses per tile (MMA M)
 constexpr int kTK = 128;            // variables per stage (128 bytes a row in shared memory)
 constexpr int kStages = 4;
+constexpr int kAccBufs = 2;         // TMEM accumulators (segment j uses j % 2)
 constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
@@ -50,9 +63,12 @@ constexpr uint8_t kE2M1One = 0x2, kE2M1MinusOne = 0xA;
 struct DenseHeader {
     unsigned long long full[kStages];
     unsigned long long empty[kStages];
-    unsigned long long done;
+    unsigned long long acc_full[kAccBufs];
+    unsigned long long acc_empty[kAccBufs];
     uint32_t tmem;
     int abort;
+    int epi_fail;  // written only by the epilogue warps, read after their barrier
+    int last;      // this CTA finishes the split tile
     unsigned long long colsum[256];
 };
 static_assert(sizeof(DenseHeader) <= kHeader, "dense header does not fit");
@@ -88,6 +104,23 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// The same, giving up early once another role of the block has aborted.
+__device__ __forceinline__ bool mbar_wait_abort(unsigned long long *bar, uint32_t parity, long long limit,
+                                                const int *abort) {
+    for (long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023) == 1023 && *(volatile const int *)abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier of the four epilogue warps (128 threads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             unsigned long long *bar) {
@@ -162,35 +195,69 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One segment of a CTA's work: k-steps [ka, kb) of tile `tile`; tr is the
+// split-tile index (-1 for a whole tile) and piece the part of it.
+struct DenseSeg {
+    int tile, ka, kb, tr, piece;
+};
+
+__device__ __forceinline__ int seg_count(const DenseSched &d, int c) {
+    return d.full + (c < d.tail_ctas ? 1 : 0);
+}
+
+__device__ __forceinline__ DenseSeg seg_at(const DenseSched &d, int c, int j) {
+    DenseSeg g;
+    if (j < d.full) {
+        g.tile = j * (int)gridDim.x + c;
+        g.ka = 0;
+        g.kb = d.kt_count;
+        g.tr = -1;
+        g.piece = 0;
+        return g;
+    }
+    g.tr = c / d.split;
+    g.piece = c % d.split;
+    g.tile = d.full * (int)gridDim.x + g.tr;
+    g.ka = (int)((long long)g.piece * d.kt_count / d.split);
+    g.kb = (int)((long long)(g.piece + 1) * d.kt_count / d.split);
+    return g;
+}
+
 __global__ void __launch_bounds__(kDenseThreads, 1)
     k_dense_eval(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const float *__restrict__ target, const uint32_t *__restrict__ wgt, int kt_count,
-                 int ntile, int tmem_cols, int nb, unsigned long long *__restrict__ cost,
+                 const float *__restrict__ target, const uint32_t *__restrict__ wgt, DenseSched d,
+                 int tmem_cols, int nb, unsigned long long *__restrict__ cost, const float *__restrict__ ptgt,
+                 uint32_t *__restrict__ pmask, unsigned int *__restrict__ part_cnt,
                  unsigned int *__restrict__ errflag) {
     extern __shared__ uint8_t dsm_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
     DenseHeader *H = reinterpret_cast<DenseHeader *>(base);
     uint8_t *stages = base + kHeader;
+    const int ntile = d.ntile;
     const uint32_t a_bytes = kTM * kTK;
     const uint32_t b_bytes = (uint32_t)ntile * kTK;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kTM;
-    const int n0 = blockIdx.y * ntile;
+    const int cta = blockIdx.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&H->full[s], 1);
             mbar_init(&H->empty[s], 1);
         }
-        mbar_init(&H->done, 1);
+        for (int b = 0; b < kAccBufs; ++b) {
+            mbar_init(&H->acc_full[b], 1);
+            mbar_init(&H->acc_empty[b], 4);  // one arrive per epilogue warp
+        }
         H->abort = 0;
+        H->epi_fail = 0;
+        H->last = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int c = threadIdx.x; c < 256; c += blockDim.x) H->colsum[c] = 0ull;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&H->tmem)),
-                     "r"(tmem_cols)
+                     "r"(kAccBufs * tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -198,89 +265,188 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = H->tmem;
+    const int nseg = seg_count(d, cta);
 
     if (warp == 0 && lane == 0) {
         // producer: TMA loads of the A (clause rows) and B (assignment rows)
-        // tiles; the A tiles are prefetched into L2 kPrefetch k-tiles ahead
-        // (x = kt * 128 bytes: 16-byte aligned)
-        for (int kt = 0; kt < kt_count && kt < kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kTK, m0);
-        int issued = 0;
-        for (int kt = 0; kt < kt_count; ++kt) {
-            const int s = kt % kStages;
-            if (kt + kPrefetch < kt_count) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kTK, m0);
-            if (kt >= kStages) {
-                const uint32_t parity = (uint32_t)((kt / kStages - 1) & 1);
-                if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, kSpin)) {
-                    H->abort = 1;
-                    atomicOr(errflag, 1u);
-                    break;
+        // tiles of every segment in turn; the A tiles are prefetched into L2
+        // kPrefetch k-tiles ahead within a segment (x = kt * 128 codes: 64
+        // bytes, 16-byte aligned)
+        int it = 0;
+        bool stop = false;
+        for (int j = 0; j < nseg && !stop; ++j) {
+            const DenseSeg g = seg_at(d, cta, j);
+            const int m0 = (g.tile % d.tiles_m) * kTM, n0 = (g.tile / d.tiles_m) * ntile;
+            for (int kt = g.ka; kt < g.kb && kt < g.ka + kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kTK, m0);
+            for (int kt = g.ka; kt < g.kb; ++kt) {
+                const int s = it % kStages;
+                if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kTK, m0);
+                if (it >= kStages) {
+                    const uint32_t parity = (uint32_t)((it / kStages - 1) & 1);
+                    if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, kSpin)) {
+                        H->abort = 1;
+                        atomicOr(errflag, 1u);
+                        stop = true;
+                        break;
+                    }
                 }
+                uint8_t *sa = stages + (size_t)s * stage_bytes;
+                // the transaction count of a packed-type load is the bytes it
+                // reads (two codes a byte), half what it writes to shared memory
+                mbar_expect_tx(&H->full[s], stage_bytes / 2);
+                tma_load_2d(sa, &tmA, kt * kTK, m0, &H->full[s]);
+                tma_load_2d(sa + a_bytes, &tmB, kt * kTK, n0, &H->full[s]);
+                ++it;
             }
-            uint8_t *sa = stages + (size_t)s * stage_bytes;
-            // the transaction count of a packed-type load is the bytes it
-            // reads (two codes a byte), half what it writes to shared memory
-            mbar_expect_tx(&H->full[s], stage_bytes / 2);
-            tma_load_2d(sa, &tmA, kt * kTK, m0, &H->full[s]);
-            tma_load_2d(sa + a_bytes, &tmB, kt * kTK, n0, &H->full[s]);
-            issued = kt + 1;
         }
         // every issued copy has landed before the block may exit
-        for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
-            if (!mbar_wait(&H->full[kt % kStages], (uint32_t)((kt / kStages) & 1), kSpin)) atomicOr(errflag, 2u);
+        for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
+            if (!mbar_wait(&H->full[i % kStages], (uint32_t)((i / kStages) & 1), kSpin)) atomicOr(errflag, 2u);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer: segment j accumulates into TMEM buffer j % 2 once the
+        // epilogue has read what the segment before last left there
         const uint32_t idesc = idesc_e2m1(ntile);
-        for (int kt = 0; kt < kt_count; ++kt) {
-            const int s = kt % kStages;
-            if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((kt / kStages) & 1), kSpin)) {
+        int it = 0;
+        bool stop = false;
+        for (int j = 0; j < nseg && !stop; ++j) {
+            const DenseSeg g = seg_at(d, cta, j);
+            const int buf = j % kAccBufs;
+            if (j >= kAccBufs &&
+                !mbar_wait_abort(&H->acc_empty[buf], (uint32_t)((j / kAccBufs - 1) & 1), 4 * kSpin, &H->abort)) {
                 H->abort = 1;
                 atomicOr(errflag, 1u);
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(stages + (size_t)s * stage_bytes);
-            const uint64_t adesc = smem_desc_sw128(sa);
-            const uint64_t bdesc = smem_desc_sw128(sa + a_bytes);
-#pragma unroll
-            for (int kk = 0; kk < kTK / 32; ++kk)  // K = 32 bytes per MMA: +2 in the 16-byte address field
-                mma_f8f6f4(tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt | kk) != 0);
-            mma_commit(&H->empty[s]);
-        }
-        mma_commit(&H->done);  // arrives once every MMA issued above has completed
-    } else if (warp >= 2) {
-        // epilogue: TMEM lane quarter q holds clause rows m0 + 32q .. + 31
-        const bool ok = mbar_wait(&H->done, 0u, 4 * kSpin);
-        if (!ok) atomicOr(errflag, 4u);
-        tc_fence_after();
-        const int q = warp & 3;
-        const int row = m0 + 32 * q + lane;
-        const float tgt = __ldg(target + row);
-        const uint32_t w = __ldg(wgt + row);
-        if (ok && !*(volatile int *)&H->abort) {
-            for (int c0 = 0; c0 < ntile; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-                uint32_t mine = 0;
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const uint32_t hit = (__uint_as_float(v[c]) == tgt) ? w : 0u;
-                    const uint32_t sum = __reduce_add_sync(0xffffffffu, hit);
-                    if (lane == c) mine = sum;
+            const uint32_t acc = tmem + (uint32_t)(buf * tmem_cols);
+            for (int kt = g.ka; kt < g.kb; ++kt) {
+                const int s = it % kStages;
+                if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((it / kStages) & 1), kSpin)) {
+                    H->abort = 1;
+                    atomicOr(errflag, 1u);
+                    stop = true;
+                    break;
                 }
-                if (mine) atomicAdd(&H->colsum[c0 + lane], (unsigned long long)mine);
+                tc_fence_after();
+                const uint32_t sa = smem_u32(stages + (size_t)s * stage_bytes);
+                const uint64_t adesc = smem_desc_sw128(sa);
+                const uint64_t bdesc = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+                for (int kk = 0; kk < kTK / 32; ++kk)  // K = 32 codes per MMA: +2 in the 16-byte address field
+                    mma_f8f6f4(acc, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt != g.ka || kk != 0) ? 1u : 0u);
+                mma_commit(&H->empty[s]);
+                ++it;
             }
+            if (stop) break;
+            mma_commit(&H->acc_full[buf]);  // arrives once every MMA of the segment has completed
+        }
+    } else if (warp >= 2) {
+        // epilogue: TMEM lane quarter q (= warp % 4) holds clause rows
+        // m0 + 32q .. + 31 of the segment's tile
+        const int q = warp & 3;
+        const int r = 32 * q + lane;  // row within the tile
+        const int etid = threadIdx.x - 64;
+        for (int j = 0; j < nseg; ++j) {
+            const DenseSeg g = seg_at(d, cta, j);
+            const int buf = j % kAccBufs;
+            const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / kAccBufs) & 1), 4 * kSpin, &H->abort);
+            if (!ok) H->epi_fail = 1;
+            epi_sync();
+            if (H->epi_fail) {  // the same decision in all four warps
+                if (etid == 0) atomicOr(errflag, 4u);
+                H->abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const int m0 = (g.tile % d.tiles_m) * kTM, n0 = (g.tile / d.tiles_m) * ntile;
+            const float tgt = __ldg(target + m0 + r);
+            const uint32_t w = __ldg(wgt + m0 + r);
+            const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * tmem_cols);
+            if (g.tr < 0) {
+                // a whole tile: the sums are complete; count the unsat
+                // clauses per column
+                for (int c0 = 0; c0 < ntile; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(acc + (uint32_t)c0, v);
+                    uint32_t mine = 0;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const uint32_t hit = (__uint_as_float(v[c]) == tgt) ? w : 0u;
+                        const uint32_t sum = __reduce_add_sync(0xffffffffu, hit);
+                        if (lane == c) mine = sum;
+                    }
+                    if (mine) atomicAdd(&H->colsum[c0 + lane], (unsigned long long)mine);
+                }
+            } else {
+                // a piece of a split tile: bit c of word [chunk][row] says
+                // that every literal of the row's clause in this piece's
+                // k-range is false under assignment chunk * 32 + c
+                const int nch = (ntile + 31) / 32;  // columns past ntile are never flushed
+                const size_t slot = (size_t)g.tr * d.split + g.piece;
+                const float ptg = __ldg(ptgt + slot * kTM + r);
+                uint32_t bits[8];
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    bits[ch] = 0u;
+                    if (ch < nch) {
+                        uint32_t v[32];
+                        tmem_ld32(acc + (uint32_t)(32 * ch), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) bits[ch] |= (__uint_as_float(v[c]) == ptg ? 1u : 0u) << c;
+                        pmask[(slot * nch + ch) * kTM + r] = bits[ch];
+                    }
+                }
+                __threadfence();  // this CTA's bits before its count
+                epi_sync();
+                if (etid == 0) H->last = atomicAdd(part_cnt + g.tr, 1u) == (unsigned)(d.split - 1);
+                epi_sync();
+                if (H->last) {
+                    __threadfence();
+                    for (int pc = 0; pc < d.split; ++pc) {
+                        if (pc == g.piece) continue;
+                        const uint32_t *other = pmask + ((size_t)g.tr * d.split + pc) * nch * kTM + r;
+#pragma unroll
+                        for (int ch = 0; ch < 8; ++ch)
+                            if (ch < nch) bits[ch] &= __ldcg(other + (size_t)ch * kTM);
+                    }
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) {
+                        if (ch < nch) {
+                            uint32_t mine = 0;
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                const uint32_t hit = ((bits[ch] >> c) & 1u) ? w : 0u;
+                                const uint32_t hs = __reduce_add_sync(0xffffffffu, hit);
+                                if (lane == c) mine = hs;
+                            }
+                            if (mine) atomicAdd(&H->colsum[32 * ch + lane], (unsigned long long)mine);
+                        }
+                    }
+                    if (etid == 0) part_cnt[g.tr] = 0u;  // ready for the next launch
+                }
+            }
+            // the accumulator buffer is free for the segment after next
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&H->acc_empty[buf]);
+            // add the tile's column sums to the costs
+            epi_sync();
+            for (int cc = etid; cc < ntile; cc += 128) {
+                const unsigned long long cs = H->colsum[cc];
+                if (cs) {
+                    if (n0 + cc < nb) atomicAdd(cost + n0 + cc, cs);
+                    H->colsum[cc] = 0ull;
+                }
+            }
+            epi_sync();
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (!H->abort)
-        for (int c = threadIdx.x; c < ntile; c += blockDim.x) {
-            const int col = n0 + c;
-            if (col < nb && H->colsum[c]) atomicAdd(cost + col, H->colsum[c]);
-        }
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * tmem_cols)
+                     : "memory");
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier that
@@ -294,6 +460,37 @@ __global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (!mbar_wait(&bar, 0u, spins)) atomicOr(errflag, 8u);
     }
+}
+
+// Per-piece targets of the split tiles: for split tile tr, piece p and row
+// r, minus the number of the clause's literals whose variable lies in the
+// piece's k-range [p * kt / split, (p + 1) * kt / split) x 128 (NaN for
+// padding rows and for clauses that never count).
+__global__ void k_dense_piece_targets(DevInst I, const float *__restrict__ target, DenseSched d, int grid,
+                                      float *__restrict__ ptgt) {
+    const int tr = blockIdx.x, r = threadIdx.x;  // kTM threads
+    const int tile = d.full * grid + tr;
+    const long long j = (long long)(tile % d.tiles_m) * kTM + r;
+    float out[4];
+    const bool live = j < I.m && !isnan(target[j]);
+    for (int p = 0; p < 4; ++p) out[p] = live ? 0.0f : __int_as_float(0x7fc00000);
+    if (live) {
+        int beg, end;
+        if (I.kfix > 0) {
+            beg = (int)j * I.kfix;
+            end = beg + I.kfix;
+        } else {
+            beg = I.coff[j];
+            end = I.coff[j + 1];
+        }
+        for (int q = beg; q < end; ++q) {
+            const int kt = (I.lit[q] >> 1) / kTK;
+            int p = 0;
+            while (p + 1 < d.split && (long long)(p + 1) * d.kt_count / d.split <= kt) ++p;
+            out[p] -= 1.0f;
+        }
+    }
+    for (int p = 0; p < d.split; ++p) ptgt[((size_t)tr * d.split + p) * kTM + r] = out[p];
 }
 
 // W^T in packed e2m1: row j (n_pad / 2 bytes) holds +1 / -1 at the columns
@@ -443,6 +640,37 @@ cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int
     return cudaGetLastError();
 }
 
+// Whole tiles one per CTA when they fit one wave of one CTA per SM; with
+// more tiles, equal whole-tile shares per CTA, and a leftover of at most
+// half a wave split into up to 4 k-step pieces per tile (a larger leftover
+// runs as a last partial wave of whole tiles).
+DenseSched dense_plan(const DenseDev &d, int ntile, int *grid) {
+    DenseSched p{};
+    p.kt_count = d.n_pad / kTK;
+    p.tiles_m = d.m_pad / kTM;
+    p.ntile = ntile;
+    p.full = 1;
+    p.split = 1;
+    const int T = p.tiles_m * (d.tmB_rows / ntile);
+    const int G = d.sm_count > 0 ? d.sm_count : 152;
+    *grid = T;
+    if (T > G) {
+        const int full = T / G, rest = T - full * G;
+        int split = rest > 0 ? G / rest : 0;
+        if (split > 4) split = 4;
+        if (split > p.kt_count) split = p.kt_count;
+        // a piece's sums must fit int16: at most 255 k-steps of 128
+        if (rest > 0 && split >= 2 && (p.kt_count + split - 1) / split <= 255) {
+            p.full = full;
+            p.tail = rest;
+            p.split = split;
+            p.tail_ctas = rest * split;
+            *grid = G;
+        }
+    }
+    return p;
+}
+
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st) {
     const int ntile = d.tmB_ntile;
     cudaError_t e;
@@ -451,14 +679,24 @@ cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaSt
     if (e) return e;
     int tmem_cols = 32;
     while (tmem_cols < ntile) tmem_cols <<= 1;
-    dim3 grid((unsigned)(d.m_pad / kTM), (unsigned)(d.tmB_rows / ntile));
-    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, d.n_pad / kTK, ntile,
-                                                   tmem_cols, nb, reinterpret_cast<unsigned long long *>(cost),
-                                                   d.errflag);
+    int grid = 0;
+    const DenseSched p = dense_plan(d, ntile, &grid);
+    if (p.tail > 0 && (p.tail * p.split > d.ptgt_slots || p.tail > d.part_cnts || ntile != d.pmask_ntile))
+        return cudaErrorInvalidValue;
+    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, p, tmem_cols, nb,
+                                                   reinterpret_cast<unsigned long long *>(cost), d.ptgt, d.pmask,
+                                                   d.part_cnt, d.errflag);
     return cudaGetLastError();
 }
 
 size_t smem_max_dense() { return dense_smem_bytes(256); }
+
+cudaError_t launch_dense_piece_targets(const DevInst &I, const DenseDev &d, const DenseSched &p, int grid,
+                                       cudaStream_t st) {
+    if (p.tail <= 0) return cudaSuccess;
+    k_dense_piece_targets<<<p.tail, kTM, 0, st>>>(I, d.target, p, grid, d.ptgt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wait_selftest(long long spins, unsigned int *errflag, cudaStream_t st) {
     k_wait_selftest<<<1, 32, 0, st>>>(spins, errflag);

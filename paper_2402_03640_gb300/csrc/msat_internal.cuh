@@ -99,6 +99,21 @@ struct DevState {
 // [m_pad][n_pad] in packed e2m1 (n_pad / 2 bytes a row), per-row target
 // -len_j (NaN: never unsat), 32-bit weights, the packed e2m1 assignment
 // batch X^T [rows][n_pad] and their TMA descriptors.
+// Work split of one dense launch: tile t covers clause rows
+// (t % tiles_m) * 128 and assignment columns (t / tiles_m) * ntile; CTA c
+// takes whole tiles j * grid + c for j < full, then (c < tail_ctas) piece
+// c % split of split tile c / split: k-steps [piece * kt_count / split,
+// (piece + 1) * kt_count / split) of tile full * grid + c / split.
+struct DenseSched {
+    int kt_count;   // k-steps (128 variables) per tile
+    int tiles_m;
+    int ntile;      // assignments per tile
+    int full;
+    int tail;       // split tiles
+    int split;      // pieces per split tile
+    int tail_ctas;  // tail * split
+};
+
 struct DenseDev {
     uint8_t *Wt = nullptr;
     float *target = nullptr;
@@ -108,6 +123,16 @@ struct DenseDev {
     size_t xt_bytes = 0;
     int tmB_rows = 0, tmB_ntile = 0;
     unsigned int *errflag = nullptr;
+    // split tiles: per-piece targets [tile][piece][row], the pieces' unsat
+    // bits [tile][piece][column / 32][row] and the pieces counted in per
+    // tile (kept zeroed); plan and plan_grid: what the targets were made for
+    float *ptgt = nullptr;
+    uint32_t *pmask = nullptr;
+    unsigned int *part_cnt = nullptr;
+    int ptgt_slots = 0, part_cnts = 0, pmask_ntile = 0;
+    DenseSched plan{};
+    int plan_grid = -1;
+    int sm_count = 0;
     CUtensorMap tmA, tmB;
 };
 
@@ -271,6 +296,9 @@ cudaError_t launch_dense_convert(const DenseDev &d, const int8_t *a, int n, int 
                                  cudaStream_t st);
 cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int nb, long long *cost,
                                    cudaStream_t st);
+DenseSched dense_plan(const DenseDev &d, int ntile, int *grid);
+cudaError_t launch_dense_piece_targets(const DevInst &I, const DenseDev &d, const DenseSched &p, int grid,
+                                       cudaStream_t st);
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st);
 cudaError_t launch_wait_selftest(long long spins, unsigned int *errflag, cudaStream_t st);
 

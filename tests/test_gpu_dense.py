@@ -69,6 +69,21 @@ def test_dense_config1_full_size(pkg, oracle):
     _check(pkg, oracle, cnf, [256])
 
 
+def test_dense_split_tiles(pkg, oracle):
+    """More clause tiles than SMs: the leftover tiles are split into k-step
+    pieces, each testing its partial sums against per-piece targets, and the
+    pieces' bits are ANDed.  Mixed lengths and weights; clauses spanning
+    every piece, a tautology, an empty clause and a 1024-literal clause in
+    the split tiles; one and two assignment tiles."""
+    base = zipf_weighted(5000, 20000, seed=7)
+    rng = np.random.default_rng(8)
+    extra = [[int(sg) * (1 + 10 * i) for i, sg in enumerate(rng.choice([-1, 1], size=500))] for _ in range(3)]
+    extra += [[5, -5, 77], [], [4999, -5000], list(range(1, 1025)), list(range(-5000, 0, 5))]
+    w = list(base.weights if base.weights is not None else np.ones(base.m, np.int64)) + [3] * len(extra)
+    cnf = Cnf.from_clauses(5000, base.clauses() + extra, weights=w)
+    _check(pkg, oracle, cnf, [100, 300])
+
+
 def test_evaluate_current_x_both_backends(pkg, oracle):
     """The rounded batch of the solver's own x: dense, sparse and the cost the
     step kernels report agree with the oracle after a few steps."""
