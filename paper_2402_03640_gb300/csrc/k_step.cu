@@ -1144,6 +1144,18 @@ __global__ void __launch_bounds__(kThreads)
     vars_body<VS, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
 }
 
+// The same pass held to 64 registers a thread, so that four 256-thread
+// blocks are resident per SM instead of three: used for the shapes where
+// that costs no spills (stored w*f with up to 4 restarts a task, or up to 2
+// restarts a task).  The pass is latency-bound on its gathers, so the
+// extra resident warps hide more of that latency.
+template <int VS, int KFIX, bool STORE>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_backward_light_occ4(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                          const float *__restrict__ gscale, float *__restrict__ grad_out) {
+    vars_body<VS, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
+}
+
 template <int VS, int VU, int KFIX, bool STORE>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
                                      int mode, const float *t_ovr, const float *gscale,
@@ -1157,8 +1169,12 @@ static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const 
     }
     const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
     const size_t smem = light_smem_bytes(I.task_cap, VS);
-    k_backward_light<VS, KFIX, STORE><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
-                                                                                 gscale, grad_out);
+    if constexpr ((STORE && VS <= 4) || VS <= 2)
+        k_backward_light_occ4<VS, KFIX, STORE><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
+                                                                                      gscale, grad_out);
+    else
+        k_backward_light<VS, KFIX, STORE><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
+                                                                                     gscale, grad_out);
     return cudaGetLastError();
 }
 
