@@ -586,7 +586,10 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     S->cfg = cfg;
     S->work_cap = cfg.batch_mlits > 0 ? (int64_t)cfg.batch_mlits * 1000000 : 0;
     S->fwd_vw = auto_fwd_vw(B);
-    S->stage_vw = auto_stage_vw(B);
+    // two restarts a leaf task: the batched variable pass then fits four
+    // resident blocks per SM (63 registers) instead of two at four restarts
+    // (86); launch shapes never change a result bit
+    S->stage_vw = B < 2 ? B : 2;
     S->task_cap = std::max(kTaskCap, B / S->stage_vw);
     const int M = cfg.max_slots + 1;
     // builders: half the host's hardware threads, 1 to 8
