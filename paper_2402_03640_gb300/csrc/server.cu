@@ -585,7 +585,10 @@ extern "C" int msat_server_create(msat_server **out, const msat_server_config *c
     }
     S->cfg = cfg;
     S->work_cap = cfg.batch_mlits > 0 ? (int64_t)cfg.batch_mlits * 1000000 : 0;
-    S->fwd_vw = auto_fwd_vw(B);
+    // four restarts a thread in the batched clause pass (74 registers, three
+    // resident blocks per SM; eight take 92 and two blocks) -- measured on
+    // the k in {3,4,5} request stream at B = 8: 69 -> 75 instances/s
+    S->fwd_vw = B < 4 ? B : 4;
     // two restarts a leaf task: the batched variable pass then fits four
     // resident blocks per SM (63 registers) instead of two at four restarts
     // (86); launch shapes never change a result bit
