@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import ordering, pigeonhole, serving_stream, uniform_ksat, zipf_weighted  # noqa: E402
+from synth import ordering, pigeonhole, random_partial, serving_stream, uniform_ksat, zipf_weighted  # noqa: E402
 
 L2_BYTES = 129 * 2 ** 20
 
@@ -57,6 +57,10 @@ SERVE_RESTARTS = 8
 # cost-vs-time curves of Algorithm 1 with its time limit on the structured
 # families of Table 2 (pigeonhole PHP and ordering GT, optimum cost 1)
 STRUCTURED = "structured_cost_time"
+# the rows after the hot path: the loss normalisers of the ablation on the
+# default instance, steps to the best cost, the quick f_j > 0 reading against
+# the exact test, and a partial MaxSAT instance
+NEXT_ROWS = "next_rows_loss_partial"
 # workloads whose step also runs the dense tensor-core evaluation of the rounded batch
 DENSE_EVAL = {"ksat3_n5000_m21500_b256"}
 LR = 1e-4
@@ -213,6 +217,10 @@ def run_reference(args):
     if args.workload == STRUCTURED:
         print(json.dumps({"impl": "reference", "unavailable": "the cost-vs-time curves have no oracle arm: "
                           "the oracle has no wall-clock limit"}), flush=True)
+        return 0
+    if args.workload == NEXT_ROWS:
+        print(json.dumps({"impl": "reference", "unavailable": "the ablation and partial-MaxSAT runs have no "
+                          "oracle arm: the oracle pins these rows in the tests"}), flush=True)
         return 0
     gen, B, desc = WORKLOADS[args.workload]
     cnf = gen()
@@ -656,6 +664,71 @@ def run_structured(args):
     return 0
 
 
+def run_next_rows(args):
+    """Each loss normaliser of the ablation (mean over unsat clauses, sum,
+    mean over all clauses) on the default 3-SAT instance with B = 256 for a
+    fixed number of steps through msat_solve; per run the best cost, the
+    steps to it, and at the end the quick f_j > 0 reading against the exact
+    test.  Then a partial MaxSAT instance (planted 3-SAT hard clauses, unit
+    soft clauses weighted 1..9, hard weight top = 1 + sum of soft weights)
+    solved as one weighted instance: restarts whose best cost is below top
+    satisfy every hard clause, and that cost is their soft cost."""
+    import torch
+    import paper_2402_03640_gb300 as pkg
+    from paper_2402_03640_gb300 import build as pkg_build
+
+    ws, rank, _ = dist_env()
+    torch.cuda.set_device(0 if ws == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    pkg_build.build()
+    pkg.load()
+    steps, lr = args.next_steps, 3e-2
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    cnf = WORKLOADS[DEFAULT_WORKLOAD][0]()
+    B = WORKLOADS[DEFAULT_WORKLOAD][1]
+    ablation = {}
+    for norm in ("mean_unsat", "sum_unsat", "mean_all"):
+        with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=lr, loss_norm=norm) as s:
+            r = s.solve(steps, chunk=100)
+            _, best = s.best()
+            bstep = s.best_step()
+            hu, dg = s.heuristic_gap()
+        b = int(np.argmin(best))
+        ablation[norm] = {"steps": int(r["steps"]), "ms_per_step": 1e3 * r["elapsed_s"] / max(1, r["steps"]),
+                          "best_cost": int(best.min()), "mean_best_cost": float(best.mean()),
+                          "steps_to_best": int(bstep[b]),
+                          "quick_reading_unsat_mean": float(hu.mean()),
+                          "quick_reading_disagreements_mean": float(dg.mean())}
+    n_p, m_hard, m_soft, Bp = 2000, 6000, 2000, 64
+    pcnf = random_partial(n_p, m_hard, m_soft, seed=0)
+    top = int(pcnf.weights[:m_hard].max())
+    with pkg.Solver.from_cnf(pcnf, restarts=Bp, seed_x=1, lr=lr) as s:
+        r = s.solve(steps, chunk=100)
+        _, best = s.best()
+        bstep = s.best_step()
+    ok = best < top
+    bmin = int(best.min())
+    # a cost is top x (hard clauses violated) + soft cost, the soft cost < top
+    partial = {"n": n_p, "hard_clauses": m_hard, "soft_clauses": m_soft, "top": top, "restarts": Bp,
+               "steps": int(r["steps"]), "ms_per_step": 1e3 * r["elapsed_s"] / max(1, r["steps"]),
+               "best_cost": bmin, "best_hard_violated": bmin // top, "best_soft_cost": bmin % top,
+               "restarts_with_hard_satisfied": int(ok.sum()),
+               "steps_to_best": int(bstep[int(np.argmin(best))])}
+    clk = clocks.stop()
+    line = {"metric": "best cost after a fixed number of steps (mean-over-unsat loss)",
+            "value": ablation["mean_unsat"]["best_cost"], "unit": "weighted unsat clauses", "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": ablation["mean_unsat"]["ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": NEXT_ROWS, "instance": DEFAULT_WORKLOAD, "restarts": B, "lr": lr,
+                       "partial_instance": f"planted 3-SAT n={n_p}, {m_hard} hard clauses (seed 0), "
+                                           f"{m_soft} unit soft clauses weighted 1..9"},
+            "loss_ablation": ablation, "partial_maxsat": partial, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     import torch
     import paper_2402_03640_gb300 as pkg
@@ -721,8 +794,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SERVING, STRUCTURED],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SERVING, STRUCTURED, NEXT_ROWS],
                     default=DEFAULT_WORKLOAD)
+    ap.add_argument("--next-steps", type=int, default=2000,
+                    help="steps of each run of the ablation / partial MaxSAT workload")
     ap.add_argument("--time-limit", type=float, default=1.0,
                     help="seconds per instance of the structured cost-vs-time workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -738,6 +813,8 @@ def main():
         return run_serving(args)
     if args.workload == STRUCTURED:
         return run_structured(args)
+    if args.workload == NEXT_ROWS:
+        return run_next_rows(args)
     return run_ours(args)
 
 
