@@ -180,9 +180,12 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
                                              " is below 1");
 
     // canonical clauses: drop a literal equal to an earlier one of its clause
+    // (the first occurrence keeps its place); seen[literal] is the last
+    // clause that kept it, so a clause costs O(its length)
     std::vector<int32_t> coff((size_t)m + 1);
     std::vector<int32_t> lit;
     lit.reserve((size_t)raw);
+    std::vector<int32_t> seen((size_t)n_vars * 2, -1);
     int64_t wsum = 0;
     int32_t max_len = 0;
     coff[0] = 0;
@@ -191,10 +194,9 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
         for (int64_t p = clause_off[j]; p < clause_off[j + 1]; ++p) {
             const int32_t l = lits[p];
             const int32_t packed = ((std::abs(l) - 1) << 1) | (l < 0 ? 1 : 0);
-            bool dup = false;
-            for (size_t r = start; r < lit.size(); ++r)
-                if (lit[r] == packed) { dup = true; break; }
-            if (!dup) lit.push_back(packed);
+            if (seen[(size_t)packed] == (int32_t)j) continue;
+            seen[(size_t)packed] = (int32_t)j;
+            lit.push_back(packed);
         }
         const int32_t len = (int32_t)(lit.size() - start);
         if (len > kMaxClauseLen)
@@ -329,15 +331,19 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     c->wsum = wsum;
     c->clen.resize((size_t)m);
     c->taut.assign((size_t)m, 0);
-    for (int64_t j = 0; j < m; ++j) {
-        const int32_t b0 = coff[(size_t)j], b1 = coff[(size_t)j + 1];
-        c->clen[(size_t)j] = b1 - b0;
-        for (int32_t p = b0; p < b1 && !c->taut[(size_t)j]; ++p)
-            for (int32_t q = p + 1; q < b1; ++q)
-                if ((lit[(size_t)p] >> 1) == (lit[(size_t)q] >> 1)) {
-                    c->taut[(size_t)j] = 1;
-                    break;
-                }
+    {
+        // after the repeats are gone, a variable seen twice in a clause
+        // appears as x and not x: the clause can never be unsat
+        std::vector<int32_t> vseen((size_t)n_vars, -1);
+        for (int64_t j = 0; j < m; ++j) {
+            const int32_t b0 = coff[(size_t)j], b1 = coff[(size_t)j + 1];
+            c->clen[(size_t)j] = b1 - b0;
+            for (int32_t p = b0; p < b1; ++p) {
+                const int32_t v = lit[(size_t)p] >> 1;
+                if (vseen[(size_t)v] == (int32_t)j) c->taut[(size_t)j] = 1;
+                vseen[(size_t)v] = (int32_t)j;
+            }
+        }
     }
     if (weights) c->wts.assign(weights, weights + m);
 
