@@ -284,7 +284,7 @@ def run_ours(args):
     flush_buf = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda") if flush else None
 
     # launch shapes from the library's autotuner (they never change a result bit)
-    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, tune=True)
+    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, tune=True, f_mode=args.f_mode)
     stream = torch.cuda.current_stream()
     dense = args.workload in DENSE_EVAL
     dense_cost = torch.empty(B, dtype=torch.int64, device="cuda")
@@ -447,7 +447,7 @@ def run_ours(args):
     hcost = torch.empty(B, dtype=torch.int64).pin_memory()
     dcost = torch.empty(B, dtype=torch.int64, device="cuda")
     t0 = time.perf_counter()
-    s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR)
+    s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, f_mode=args.f_mode)
     t_create = time.perf_counter() - t0
     for _ in range(e2e_steps):
         if dense:  # the final sparse evaluation is replaced by the dense one
@@ -497,6 +497,7 @@ def run_ours(args):
                               "each step replayed from a CUDA graph of its launches" if graph_err is None
                               else "plain launches (graph capture failed: %s)" % graph_err),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "f_mode": args.f_mode,
                    "n_heavy": info["n_heavy"]},
         "roofline": roofline,
         "kernels": per_kernel,
@@ -801,6 +802,8 @@ def main():
     ap.add_argument("--time-limit", type=float, default=1.0,
                     help="seconds per instance of the structured cost-vs-time workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--f-mode", choices=("auto", "store", "recompute", "expanded"), default="auto",
+                    help="how the variable pass gets f: stored by the clause pass or recomputed")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving comparison (0: skip it on the default line)")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="Poisson arrival rate, requests/s")
