@@ -399,8 +399,10 @@ int msat_objective_noalloc(int32_t n_vars, int64_t n_clauses, const int64_t *cla
  * Serving: a request loop that runs many instances at once (continuous
  * batching).  Requests arrive with msat_submit at any time; a scheduler
  * thread admits them, oldest first, while their device memory fits the
- * budget and a slot is free, keeps every admitted instance's clause arrays
- * and optimizer state resident, and advances all of them together: each
+ * budget, a slot is free and the batch's step work stays under its cap; a
+ * pool of host threads builds the admitted instances' contexts in parallel.
+ * The server keeps every admitted instance's clause arrays and optimizer
+ * state resident and advances all of them together: each
  * iteration of Algorithm 1 for the whole slot table is one captured CUDA
  * graph (three batched kernels), replayed chunk by chunk.  An instance that
  * has taken its steps gets one final evaluation; its result is copied out
@@ -446,7 +448,7 @@ typedef struct {
     int64_t steps;        /* optimizer steps taken                       */
     int32_t n_vars;
     int32_t restarts;
-    double queue_ms;      /* submit -> admitted                          */
+    double queue_ms;      /* submit -> admitted and its context built    */
     double latency_ms;    /* submit -> result ready                      */
     int64_t best_step;    /* steps taken before the best restart's best x
                              (steps to best; 0 = the random start)        */
