@@ -46,7 +46,10 @@ WORKLOADS = {
     "ksat3_n50_m215_b1": (lambda: uniform_ksat(50, 215, 3, seed=0), 1,
                           "uniform random 3-SAT, n=50, m=215 (seed 0), B=1"),
 }
-DEFAULT_WORKLOAD = "ksat3_n5000_m21500_b256"
+# the line's value: the largest configuration on one GPU, 3-SAT n=1e6, B=16
+DEFAULT_WORKLOAD = "ksat3_n1000000_m4300000_b16"
+# measured beside it: batched restarts with the tensor-core evaluation
+DENSE_WORKLOAD = "ksat3_n5000_m21500_b256"
 # the request stream of the serving measurement: k in {3,4,5}, n log-uniform
 # in [100, 50000], ratio U[4.0, 4.6] scaled to each k's threshold, Poisson
 # arrivals; each request takes SERVE_STEPS steps with SERVE_RESTARTS restarts
@@ -165,6 +168,77 @@ def cpu_oracle_rate(cnf, B, budget_s=12.0, max_steps=200):
     return cnf.nnz * B * steps / dt, steps, dt
 
 
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_oracle_rate_threads(cnf, B, threads, budget_s=12.0, max_steps=200):
+    """Literal-evals/s of the FP32-mode oracle on `threads` host threads:
+    restarts are independent, so the B restarts are split into `threads`
+    groups (or, when B < threads, `threads` independent copies of the
+    one-restart problem run side by side), each solved by its own oracle
+    call on its own thread (the C oracle runs without the interpreter lock).
+    The oracle's arithmetic is untouched; only whole restarts are spread."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle
+    oracle.build()
+    per = max(1, B // threads)
+    t = time.perf_counter()
+    oracle.solve(cnf, per, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+    one = max(time.perf_counter() - t, 1e-4)
+    steps = int(max(1, min(max_steps, budget_s / one)))
+
+    def job(k):
+        oracle.solve(cnf, per, 1 + k, steps, mode=oracle.MODE_F32, want_hist=False, want_x=False)
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t = time.perf_counter()
+        list(ex.map(job, range(threads)))
+        dt = time.perf_counter() - t
+    return cnf.nnz * per * threads * steps / dt, steps, dt, per
+
+
+def cpu_baseline_entry(cnf, B):
+    """The oracle as it stands, timed on the host's cores: one thread, and
+    all of them (nproc) over restarts."""
+    rate, csteps, cdt = cpu_oracle_rate(cnf, B)
+    nproc = os.cpu_count() or 1
+    mt = None
+    if nproc > 1:
+        mrate, msteps, mdt, per = cpu_oracle_rate_threads(cnf, B, nproc)
+        mt = {"value": mrate, "unit": "literal-evals/s", "cores": nproc,
+              "sample": f"{nproc} threads, each {msteps} Algorithm 1 steps of the FP32-mode C oracle "
+                        f"on the full instance with {per} restart(s) ({mdt:.1f} s)"}
+    return {"value": rate, "unit": "literal-evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{csteps} Algorithm 1 steps of the FP32-mode C oracle on the full "
+                      f"instance, all {B} restarts, one host thread ({cdt:.1f} s)",
+            "cpu_model": host_cpu_model(), "host_cores": nproc, "all_cores": mt}
+
+
+def parse_shape(text):
+    """--shape FWD_VW:STAGE_VW:LIGHT_ROWS (0 = automatic) as Solver keywords."""
+    if not text:
+        return None
+    a, b, c = (int(v) for v in text.split(":"))
+    return {"fwd_vw": a, "stage_vw": b, "light_rows": c}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -224,34 +298,42 @@ def run_reference(args):
         return 0
     gen, B, desc = WORKLOADS[args.workload]
     cnf = gen()
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle
     oracle.build()
-    # restarts are independent: a bounded sample of them per step keeps the
-    # whole run within a few minutes; the metric is per literal-evaluation
+    # restarts are independent: every host core solves its own group of
+    # restarts (its own oracle call on its own thread; the C oracle runs
+    # without the interpreter lock), each step a bounded sample of the B
+    # restarts so the whole run stays within a few minutes; the metric is
+    # per literal-evaluation
+    threads = os.cpu_count() or 1
     t = time.perf_counter()
     oracle.solve(cnf, 1, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
     per_restart = max(time.perf_counter() - t, 1e-4)
-    b_sample = int(max(1, min(B, 20.0 / max(1, args.steps + args.warmup) / per_restart)))
-    for _ in range(args.warmup):
-        oracle.solve(cnf, b_sample, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
-    times = []
-    for _ in range(args.steps):
+    per = int(max(1, min(max(1, B // threads), 20.0 / max(1, args.steps + args.warmup) / per_restart)))
+
+    def run(pool, steps):
+        list(pool.map(lambda k: oracle.solve(cnf, per, 1 + k, steps, mode=oracle.MODE_F32, want_hist=False,
+                                             want_x=False), range(threads)))
+
+    with ThreadPoolExecutor(max_workers=threads) as pool:
+        run(pool, args.warmup)  # untimed
         t = time.perf_counter()
-        oracle.solve(cnf, b_sample, 1, 1, mode=oracle.MODE_F32, want_hist=False, want_x=False)
-        times.append(time.perf_counter() - t)
-    total = sum(times)
-    value = cnf.nnz * b_sample * args.steps / total
+        run(pool, args.steps)   # K steps of Algorithm 1 on every thread at once
+        total = time.perf_counter() - t
+    value = cnf.nnz * per * threads * args.steps / total
+    sample = (f"one call of {args.steps} Algorithm 1 steps (plus the final evaluation) for {per} restart(s) "
+              f"on each of {threads} host threads at once ({per * threads} restarts; the workload has {B}), "
+              f"FP32-mode C oracle, after an untimed call of {args.warmup} steps")
     line = {
         "impl": "reference", "metric": "fwd+bwd literal-evals/s", "value": value,
         "unit": "literal-evals/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "n": cnf.n, "m": cnf.m,
-                   "nnz": cnf.nnz, "restarts": B, "restarts_per_step_sampled": b_sample},
-        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps, each one Algorithm 1 iteration (plus the "
-                                   f"evaluation of the next x) for {b_sample} of the {B} restarts, "
-                                   "FP32-mode C oracle, one host thread"},
+                   "nnz": cnf.nnz, "restarts": B, "restarts_per_step_sampled": per * threads},
+        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, "cpu_model": host_cpu_model()},
         "e2e": {"value": value, "unit": "literal-evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -259,22 +341,13 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure_workload(pkg, args, workload, ws, rank, with_cpu=True, with_e2e=True):
+    """The benchmark line of one workload: K device-timed steps (graph
+    replay), per-kernel roofline, end-to-end run through the public calls
+    and the oracle's CPU baseline."""
     import torch
-    import paper_2402_03640_gb300 as pkg
-    from paper_2402_03640_gb300 import build as pkg_build
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    pkg_build.build()
-    pkg.load()
     dev = torch.cuda.current_device()
-    gen, B, desc = WORKLOADS[args.workload]
+    gen, B, desc = WORKLOADS[workload]
     cnf = gen()
     nnz = cnf.nnz
     work_per_step = nnz * B
@@ -283,10 +356,13 @@ def run_ours(args):
     flush = working_set < 2 * L2_BYTES
     flush_buf = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda") if flush else None
 
-    # launch shapes from the library's autotuner (they never change a result bit)
-    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, tune=True, f_mode=args.f_mode)
+    # launch shapes from the library's autotuner (they never change a result
+    # bit), or fixed by --shape (profiling captures skip the tuner's launches)
+    shape = parse_shape(args.shape)
+    solver = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, tune=shape is None,
+                                 f_mode=args.f_mode, **(shape or {}))
     stream = torch.cuda.current_stream()
-    dense = args.workload in DENSE_EVAL
+    dense = workload in DENSE_EVAL
     dense_cost = torch.empty(B, dtype=torch.int64, device="cuda")
     # small instances run every step of a call in one single-CTA launch:
     # time one call of K steps (per-pass timing would force the per-pass
@@ -420,7 +496,7 @@ def run_ours(args):
     if os.path.exists(tfile):
         with open(tfile) as f:
             tr = json.load(f)
-        ent = tr.get(args.workload, {}).get(dom)
+        ent = tr.get(workload, {}).get(dom)
         if ent and ent.get("kernel_hash") == kernel_hash(dom):
             traffic = ent["bytes_per_launch"]
     if per_kernel[dom]["bound"] == "tensor":
@@ -441,40 +517,14 @@ def run_ours(args):
     # optimizer step replayed from the library's CUDA graph and, on the
     # default workload, the tensor-core evaluation of the new x -- and the
     # step's B costs read back into pinned host memory
-    torch.cuda.synchronize()
-    e2e_steps = args.steps
-    h2d = cnf.off.nbytes + cnf.lits.nbytes + (0 if cnf.weights is None else cnf.weights.nbytes)
-    hcost = torch.empty(B, dtype=torch.int64).pin_memory()
-    dcost = torch.empty(B, dtype=torch.int64, device="cuda")
-    t0 = time.perf_counter()
-    s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, f_mode=args.f_mode)
-    t_create = time.perf_counter() - t0
-    for _ in range(e2e_steps):
-        if dense:  # the final sparse evaluation is replaced by the dense one
-            s2.step_async(1, final_eval=False, graph=True)
-            s2.evaluate_x("dense", out=dcost)
-            hcost.copy_(dcost, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-        else:
-            s2.step(1, want_loss=False, graph=True)
-    t1 = time.perf_counter()
-    s2.close()
-    e_max, e_units = replicas.combine(t1 - t0, float(work_per_step * e2e_steps),
-                                      device="cuda" if ws > 1 else None)
-    e2e_value = e_units / e_max
+    e2e = measure_e2e(pkg, cnf, B, args, dense, ws, dict(solver.tuning or shape or {})) if with_e2e else None
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        rate, csteps, cdt = cpu_oracle_rate(cnf, B)
-        cpu = {"value": rate, "unit": "literal-evals/s", "cores": 1, "kind": "oracle",
-               "sample": f"{csteps} Algorithm 1 steps of the FP32-mode C oracle on the full "
-                         f"instance, all {B} restarts, one host thread ({cdt:.1f} s)"}
+    if rank == 0 and with_cpu and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(cnf, B)
 
     launches = prof["forward"][0] + prof["backward"][0] + prof["evaluate"][0] + prof["other"][0]
     info = solver.info()
-    serving = None
-    if args.workload == DEFAULT_WORKLOAD and args.serve_requests > 0:
-        serving = serve_compare(pkg, args.serve_requests, args.serve_rate, rank=rank, world=ws)
     _, cost = solver.step(0, want_loss=False)
     dense_ok = None
     if dense:
@@ -486,7 +536,7 @@ def run_ours(args):
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "ms_per_step_plain_launches": None if plain_ms is None else plain_ms / args.steps,
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n": cnf.n, "m": cnf.m,
+        "config": {"workload": workload, "description": desc, "n": cnf.n, "m": cnf.m,
                    "nnz": nnz, "restarts": B, "lr": LR,
                    "l2": ("flushed (256 MiB write) before the timed call, whose K steps run in one "
                           "single-CTA launch with the state in shared memory" if small else
@@ -503,23 +553,131 @@ def run_ours(args):
         "kernels": per_kernel,
         "cpu_baseline": cpu,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": "literal-evals/s", "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": B * 8, "steps": e2e_steps, "create_ms": 1e3 * t_create,
-                "note": "msat_create from host arrays once inside the timed region (create_ms), then "
-                        "per step " +
-                        ("msat_step(1) replayed from the library's CUDA graph without its final "
-                         "evaluation, msat_evaluate_x on the tensor cores, and the B costs copied "
-                         "to pinned host memory" if dense else
-                         "msat_step(1) replayed from the library's CUDA graph with the B costs of "
-                         "its final evaluation copied to host memory")},
+        "e2e": e2e,
         "gpu_launches": launches,
-        "tuned_shape": solver.tuning and {k: solver.tuning[k] for k in ("fwd_vw", "stage_vw", "light_rows")},
+        "tuned_shape": (solver.tuning and {k: solver.tuning[k] for k in ("fwd_vw", "stage_vw", "light_rows")})
+                       or (shape and dict(shape, fixed_by="--shape")),
         "wall_s_timed": wall1 - wall0,
         "final_cost_min": int(cost.min()),
         "dense_eval_matches_sparse": dense_ok,
-        "serving": serving,
     }
     solver.close()
+    return line
+
+
+def measure_e2e(pkg, cnf, B, args, dense, ws, shape_kw):
+    """End to end through the public API with host buffers: upload the CNF
+    from host memory (context creation inside the timed region), then per
+    step the calls a user makes for the work of the timed step -- the
+    optimizer step replayed from the library's CUDA graph and, on the dense
+    evaluation workload, the tensor-core evaluation of the new x -- and the
+    step's B costs read back into host memory."""
+    import torch
+    from paper_2402_03640_gb300 import replicas
+    work_per_step = cnf.nnz * B
+    torch.cuda.synchronize()
+    e2e_steps = args.steps
+    h2d = cnf.off.nbytes + cnf.lits.nbytes + (0 if cnf.weights is None else cnf.weights.nbytes)
+    hcost = torch.empty(B, dtype=torch.int64).pin_memory()
+    dcost = torch.empty(B, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    shape_kw = {k: shape_kw[k] for k in ("fwd_vw", "stage_vw", "light_rows") if k in shape_kw}
+    s2 = pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR, f_mode=args.f_mode, **shape_kw)
+    t_create = time.perf_counter() - t0
+    for _ in range(e2e_steps):
+        if dense:  # the final sparse evaluation is replaced by the dense one
+            s2.step_async(1, final_eval=False, graph=True)
+            s2.evaluate_x("dense", out=dcost)
+            hcost.copy_(dcost, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        else:
+            s2.step(1, want_loss=False, graph=True)
+    t1 = time.perf_counter()
+    s2.close()
+    e_max, e_units = replicas.combine(t1 - t0, float(work_per_step * e2e_steps),
+                                      device="cuda" if ws > 1 else None)
+    e2e_value = e_units / e_max
+    return {"value": e2e_value, "unit": "literal-evals/s", "h2d_bytes_per_step": h2d / e2e_steps,
+            "d2h_bytes_per_step": B * 8, "steps": e2e_steps, "create_ms": 1e3 * t_create,
+            "note": "msat_create from host arrays once inside the timed region (create_ms), then "
+                    "per step " +
+                    ("msat_step(1) replayed from the library's CUDA graph without its final "
+                     "evaluation, msat_evaluate_x on the tensor cores, and the B costs copied "
+                     "to pinned host memory" if dense else
+                     "msat_step(1) replayed from the library's CUDA graph with the B costs of "
+                     "its final evaluation copied to host memory")}
+
+
+def other_configs(pkg, args, rank):
+    """The plain single instance (3-SAT n=50, m=215, 1000 steps) and the
+    weighted Zipf instance (n=2e5, m=1e6, weights 1..1000, 500 steps), B = 1,
+    x from seed 1, lr 1e-4: final and best (weighted) unsat cost and the
+    device time per step.  Their cpu_baseline leg runs the FP32-mode oracle
+    on the same configuration (one host thread) and records its time and its
+    costs, which the GPU's must equal."""
+    import torch
+    out = {}
+    for name, steps in (("ksat3_n50_m215_b1", 1000), ("zipf_n200000_m1000000_weighted_b1", 500)):
+        gen, B, desc = WORKLOADS[name]
+        cnf = gen()
+        with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=LR) as s:
+            s.step(0, want_loss=False)
+            torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step_async(steps)  # Algorithm 1: `steps` iterations, then the evaluation of x_steps
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            _, cost = s.step(0, want_loss=False)
+            _, best = s.best()
+            route = "single-CTA kernel" if s.info()["small_kernel"] else "per-pass kernels"
+        ent = {"description": desc, "n": cnf.n, "m": cnf.m, "nnz": cnf.nnz, "restarts": B, "steps": steps,
+               "lr": LR, "route": route, "ms": ms, "us_per_step": 1e3 * ms / steps,
+               "literal_evals_per_s": cnf.nnz * B * steps / (ms / 1e3),
+               "final_cost": int(cost[0]), "best_cost": int(best[0]),
+               "cost_dtype": "int64 (weighted)" if cnf.weights is not None else "int64 (count)"}
+        if rank == 0 and not args.no_cpu_baseline:
+            from oracle import oracle
+            oracle.build()
+            t = time.perf_counter()
+            ref = oracle.solve(cnf, B, 1, steps, mode=oracle.MODE_F32, lr=LR, want_x=False)
+            dt = time.perf_counter() - t
+            ent["cpu_baseline"] = {"value": cnf.nnz * B * steps / dt, "unit": "literal-evals/s", "cores": 1,
+                                   "kind": "oracle", "seconds": dt,
+                                   "sample": f"the whole run ({steps} steps, FP32-mode C oracle, one host thread)",
+                                   "final_cost": int(ref["cost_hist"][-1][0]), "best_cost": int(ref["best_cost"][0])}
+            ent["costs_equal_oracle"] = (ent["final_cost"] == ent["cpu_baseline"]["final_cost"]
+                                         and ent["best_cost"] == ent["cpu_baseline"]["best_cost"])
+        out[name] = ent
+    return out
+
+
+def run_ours(args):
+    import torch
+    import paper_2402_03640_gb300 as pkg
+    from paper_2402_03640_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    pkg_build.build()
+    pkg.load()
+    line = measure_workload(pkg, args, args.workload, ws, rank)
+    if args.workload == DEFAULT_WORKLOAD and not args.no_extras:
+        # the other configurations, each measured on its own (not part of value)
+        dense_line = measure_workload(pkg, args, DENSE_WORKLOAD, ws, rank, with_cpu=False, with_e2e=False)
+        line["dense_eval_workload"] = {k: dense_line[k] for k in (
+            "value", "unit", "ms_per_step", "ms_per_step_plain_launches", "config", "roofline", "kernels",
+            "dense_eval_matches_sparse", "tuned_shape", "clocks")}
+        line["configs"] = other_configs(pkg, args, rank)
+        if args.serve_requests > 0:
+            line["serving"] = serve_compare(pkg, args.serve_requests, args.serve_rate, rank=rank, world=ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -685,8 +843,8 @@ def run_next_rows(args):
     steps, lr = args.next_steps, 3e-2
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    cnf = WORKLOADS[DEFAULT_WORKLOAD][0]()
-    B = WORKLOADS[DEFAULT_WORKLOAD][1]
+    cnf = WORKLOADS[DENSE_WORKLOAD][0]()
+    B = WORKLOADS[DENSE_WORKLOAD][1]
     ablation = {}
     for norm in ("mean_unsat", "sum_unsat", "mean_all"):
         with pkg.Solver.from_cnf(cnf, restarts=B, seed_x=1, lr=lr, loss_norm=norm) as s:
@@ -721,7 +879,7 @@ def run_next_rows(args):
             "steps": steps, "warmup": 0, "ms_per_step": ablation["mean_unsat"]["ms_per_step"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": NEXT_ROWS, "instance": DEFAULT_WORKLOAD, "restarts": B, "lr": lr,
+            "config": {"workload": NEXT_ROWS, "instance": DENSE_WORKLOAD, "restarts": B, "lr": lr,
                        "partial_instance": f"planted 3-SAT n={n_p}, {m_hard} hard clauses (seed 0), "
                                            f"{m_soft} unit soft clauses weighted 1..9"},
             "loss_ablation": ablation, "partial_maxsat": partial, "clocks": clk}
@@ -802,9 +960,13 @@ def main():
     ap.add_argument("--time-limit", type=float, default=1.0,
                     help="seconds per instance of the structured cost-vs-time workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the other configurations and the serving comparison")
     ap.add_argument("--f-mode", choices=("auto", "store", "recompute", "expanded"), default="auto",
                     help="how the variable pass gets f: stored by the clause pass or recomputed")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--shape", default="",
+                    help="launch shape FWD_VW:STAGE_VW:LIGHT_ROWS instead of the autotuner's (0 = automatic)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving comparison (0: skip it on the default line)")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="Poisson arrival rate, requests/s")
     args = ap.parse_args()

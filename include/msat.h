@@ -381,7 +381,9 @@ int msat_profile_read(msat_ctx *ctx, msat_profile *out, int reset);
  *   restarts            B, a power of two in [1, 1024]
  *   cost_out            device int64[B]: sum of w_j over clauses with no true
  *                       literal under x' = [x > 0]
- *   loss_out            device float[B]: sum_U w f^2 / sum_U w (0 if U empty)
+ *   loss_out            device float[B]: sum_U w f^2 / sum_U w (0 if U empty);
+ *                       its sums run in another order than msat_forward's,
+ *                       with which it agrees within 1e-5 relative
  *   stream              cudaStream_t (NULL = legacy default stream)
  * Scratch: a 4 MiB array inside the library (held by every GPU that loads
  * it until the process exits); every size in the range above fits, and a

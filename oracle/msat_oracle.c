@@ -182,16 +182,22 @@ static uint64_t sm64_output(uint64_t seed, uint64_t c)
 
 uint64_t orc_splitmix64(uint64_t seed, uint64_t c) { return sm64_output(seed, c); }
 
-/* Random start of Algorithm 1: uniform on the 2^24-point grid of [-1, 1). */
-int orc_init_x(int32_t n, int32_t B, uint64_t seed, float *x /* [n][B] */)
+/* Random start of Algorithm 1: uniform on the 2^24-point grid of [-1, 1).
+ * Column b of x is restart b0 + b: output number (b0 + b) * n + i. */
+static void init_x_from(int32_t n, int32_t B, int32_t b0, uint64_t seed, float *x)
 {
-    if (n < 0 || B < 1 || (n > 0 && !x)) return ORC_EINVAL;
     for (int32_t b = 0; b < B; ++b)
         for (int32_t i = 0; i < n; ++i) {
-            uint64_t u = sm64_output(seed, (uint64_t)b * (uint64_t)n + (uint64_t)i);
+            uint64_t u = sm64_output(seed, (uint64_t)(b0 + b) * (uint64_t)n + (uint64_t)i);
             float k = (float)(uint32_t)(u >> 40);
             x[(int64_t)i * B + b] = k * 0x1p-23f - 1.0f;
         }
+}
+
+int orc_init_x(int32_t n, int32_t B, uint64_t seed, float *x /* [n][B] */)
+{
+    if (n < 0 || B < 1 || (n > 0 && !x)) return ORC_EINVAL;
+    init_x_from(n, B, 0, seed, x);
     return ORC_OK;
 }
 
@@ -609,10 +615,37 @@ int orc_step32(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, co
  *   best_cost [B], best_assign [B][n]
  *   x_final [n][B] (as double)
  */
+static int solve_from(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
+                      int32_t B, int32_t b0, uint64_t seed_x, double lr, double beta1, double beta2,
+                      double eps, int32_t steps, int32_t mode, int64_t *cost_hist, double *loss_hist,
+                      int64_t *best_cost, uint8_t *best_assign, double *x_final);
+
 int orc_solve(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
               int32_t B, uint64_t seed_x, double lr, double beta1, double beta2, double eps,
               int32_t steps, int32_t mode, int64_t *cost_hist, double *loss_hist,
               int64_t *best_cost, uint8_t *best_assign, double *x_final)
+{
+    return solve_from(n, m, off, lits, w, B, 0, seed_x, lr, beta1, beta2, eps, steps, mode,
+                      cost_hist, loss_hist, best_cost, best_assign, x_final);
+}
+
+/* The same for restarts b0 .. b0 + B - 1 of a larger run: restarts never
+ * interact (each has its own x, moments, cost and best), so a run of B'
+ * restarts equals the column-wise union of runs over any split of them. */
+int orc_solve_from(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
+                   int32_t B, int32_t b0, uint64_t seed_x, double lr, double beta1, double beta2,
+                   double eps, int32_t steps, int32_t mode, int64_t *cost_hist, double *loss_hist,
+                   int64_t *best_cost, uint8_t *best_assign, double *x_final)
+{
+    if (b0 < 0) return ORC_EINVAL;
+    return solve_from(n, m, off, lits, w, B, b0, seed_x, lr, beta1, beta2, eps, steps, mode,
+                      cost_hist, loss_hist, best_cost, best_assign, x_final);
+}
+
+static int solve_from(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
+                      int32_t B, int32_t b0, uint64_t seed_x, double lr, double beta1, double beta2,
+                      double eps, int32_t steps, int32_t mode, int64_t *cost_hist, double *loss_hist,
+                      int64_t *best_cost, uint8_t *best_assign, double *x_final)
 {
     if (B < 1 || steps < 0 || !best_cost || (mode != 0 && mode != 1)) return ORC_EINVAL;
     ocnf c;
@@ -629,7 +662,7 @@ int orc_solve(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, con
         rc = ORC_ENOMEM;
         goto done;
     }
-    orc_init_x(n, B, seed_x, x0);
+    init_x_from(n, B, b0, seed_x, x0);
 
     if (mode == 0) {
         double *x = (double *)malloc(sizeof(double) * (size_t)(nb + 1));

@@ -67,9 +67,11 @@ def _load():
                                    i32, P, P, P, P, P]
         lib.orc_solve.argtypes = [i32, i64, P, P, P, i32, u64, f64, f64, f64, f64, i32, i32,
                                   P, P, P, P, P]
+        lib.orc_solve_from.argtypes = [i32, i64, P, P, P, i32, i32, u64, f64, f64, f64, f64, i32, i32,
+                                       P, P, P, P, P]
         lib.orc_set_loss_norm.argtypes = [i32]
         for name in ("orc_init_x", "orc_cost", "orc_objective_f64", "orc_objective_f32",
-                     "orc_step32", "orc_solve", "orc_set_loss_norm"):
+                     "orc_step32", "orc_solve", "orc_solve_from", "orc_set_loss_norm"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -206,9 +208,15 @@ def step32(cnf, x, mom, vel, steps_done, best_cost, best_assign=None, update=Tru
 
 
 def solve(cnf, B: int, seed_x: int, steps: int, mode: int = MODE_F32, lr=1e-4, beta1=0.9,
-          beta2=0.999, eps=1e-8, want_hist=True, want_x=True, loss_norm="mean_unsat"):
+          beta2=0.999, eps=1e-8, want_hist=True, want_x=True, loss_norm="mean_unsat", threads=1):
     """Algorithm 1 with `steps` optimizer steps (in place of the time limit T)
-    and a final evaluation of x_steps.  Returns a dict of numpy arrays."""
+    and a final evaluation of x_steps.  Returns a dict of numpy arrays.
+    threads > 1 splits the independent restarts into groups solved side by
+    side (orc_solve_from on each group; the C code runs without the
+    interpreter lock) and joins their columns: the same arrays."""
+    if threads > 1 and B > 1:
+        return _solve_split(cnf, B, seed_x, steps, mode, lr, beta1, beta2, eps, want_hist, want_x,
+                            loss_norm, threads)
     n = cnf.n
     ch = np.empty((steps + 1, B), dtype=np.int64) if want_hist else None
     lh = np.empty((steps, B), dtype=np.float64) if want_hist else None
@@ -220,3 +228,33 @@ def solve(cnf, B: int, seed_x: int, steps: int, mode: int = MODE_F32, lr=1e-4, b
         _check(_load().orc_solve(n, cnf.m, _p(off), _p(lits), _p(w), B, seed_x, lr, beta1, beta2,
                                  eps, steps, mode, _p(ch), _p(lh), _p(best), _p(ba), _p(xf)), "solve")
     return dict(cost_hist=ch, loss_hist=lh, best_cost=best, best_assign=ba, x_final=xf)
+
+
+def _solve_part(cnf, b0, B, seed_x, steps, mode, lr, beta1, beta2, eps, want_hist, want_x):
+    n = cnf.n
+    ch = np.empty((steps + 1, B), dtype=np.int64) if want_hist else None
+    lh = np.empty((steps, B), dtype=np.float64) if want_hist else None
+    best = np.empty(B, dtype=np.int64)
+    ba = np.zeros((B, n), dtype=np.uint8)
+    xf = np.empty((n, B), dtype=np.float64) if want_x else None
+    off, lits, w = _cnf_arrays(cnf)
+    _check(_load().orc_solve_from(n, cnf.m, _p(off), _p(lits), _p(w), B, b0, seed_x, lr, beta1, beta2,
+                                  eps, steps, mode, _p(ch), _p(lh), _p(best), _p(ba), _p(xf)), "solve_from")
+    return dict(cost_hist=ch, loss_hist=lh, best_cost=best, best_assign=ba, x_final=xf)
+
+
+def _solve_split(cnf, B, seed_x, steps, mode, lr, beta1, beta2, eps, want_hist, want_x, loss_norm,
+                 threads):
+    from concurrent.futures import ThreadPoolExecutor
+    groups = min(threads, B)
+    bounds = [B * g // groups for g in range(groups + 1)]
+    with _loss_norm(loss_norm), ThreadPoolExecutor(max_workers=groups) as ex:
+        parts = list(ex.map(lambda g: _solve_part(cnf, bounds[g], bounds[g + 1] - bounds[g], seed_x, steps,
+                                                  mode, lr, beta1, beta2, eps, want_hist, want_x),
+                            range(groups)))
+    def cat(key, axis):
+        if parts[0][key] is None:
+            return None
+        return np.concatenate([p[key] for p in parts], axis=axis)
+    return dict(cost_hist=cat("cost_hist", 1), loss_hist=cat("loss_hist", 1), best_cost=cat("best_cost", 0),
+                best_assign=cat("best_assign", 0), x_final=cat("x_final", 1))

@@ -17,6 +17,12 @@
 // race on it and give wrong results.  Each call clears the finish counter
 // before its kernel; the per-block partials are written in full every call.
 //
+// The loss is summed in another order than the context path's clause pass
+// (per thread in 32-term leaves combined by the dyadic counter, then per
+// block, then over the blocks in block order), so it agrees with
+// msat_forward's loss to within 1e-5 relative, not bit for bit; the cost is
+// an exact integer sum.
+//
 // The host cannot use the symbol g_scratch as a device address; the first
 // call on each device (with that device current) asks the runtime for the
 // address with cudaGetSymbolAddress and caches it.  Make that first call
@@ -38,8 +44,8 @@ constexpr size_t kScratchBytes = 4u << 20;
 constexpr int kMaxDevices = 64;
 constexpr int kNaBlocksMax = 256;  // blocks of one launch: partials fit the scratch for B <= 1024
 
-// [0, 256): finish counter and error flag; then uint64 cost partials
-// [blocks][B]; then float loss partials [blocks][B].
+// [0, 256): finish counter; then uint64 cost partials [blocks][B]; then
+// float loss partials [blocks][B].
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -47,10 +53,11 @@ void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Every literal of clause j in order: f by the fixed summation order
 // (32-literal leaves, dyadic combination), and whether any literal is true.
+// A literal of 0 or naming no variable is skipped.
 __device__ __forceinline__ void clause_at(const int64_t *__restrict__ coff,
                                           const int32_t *__restrict__ lits,
                                           const float *__restrict__ x, int n, int B, int b,
-                                          long long j, float &f, bool &sat, bool &bad) {
+                                          long long j, float &f, bool &sat) {
     const long long beg = __ldg(coff + j), end = __ldg(coff + j + 1);
     LeafCounter<31> lc;  // any clause length the offsets can express
     lc.init();
@@ -60,10 +67,7 @@ __device__ __forceinline__ void clause_at(const int64_t *__restrict__ coff,
     for (long long p = beg; p < end; ++p) {
         const int l = __ldg(lits + p);
         const int v = (l > 0 ? l : -l) - 1;
-        if (l == 0 || v >= n) {  // malformed literal: flagged and skipped
-            bad = true;
-            continue;
-        }
+        if (l == 0 || v >= n) continue;
         const bool neg = l < 0;
         const float xv = __ldg(x + (long long)v * B + b);
         const float t = tanh_fixed(xv);
@@ -83,8 +87,9 @@ __device__ __forceinline__ void clause_at(const int64_t *__restrict__ coff,
 // multiple of B, so each thread keeps one restart; block sums per restart go
 // to the scratch partials, and the last block to finish adds them in block
 // order into cost_out and loss_out.  For B > 256 block k covers the restart
-// slice 256 * (k % (B / 256)) .. + 255.  Literals of 0 or naming no
-// variable are skipped (and raise a flag in the scratch header).
+// slice 256 * (k % (B / 256)) .. + 255.  A thread sums its loss terms in
+// 32-term leaves combined by the dyadic counter, so the rounding error grows
+// with the logarithm of its item count rather than linearly.
 __global__ void __launch_bounds__(kThreads)
     k_objective_noalloc(const int64_t *__restrict__ coff, const int32_t *__restrict__ lits,
                         const int64_t *__restrict__ w, const float *__restrict__ x, int n,
@@ -94,7 +99,6 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ float s_l[kThreads];
     __shared__ int s_last;
     unsigned int *counter = reinterpret_cast<unsigned int *>(scratch);
-    unsigned int *errflag = counter + 1;
     unsigned long long *cpart = reinterpret_cast<unsigned long long *>(scratch + 256);
     float *lpart = reinterpret_cast<float *>(cpart + (size_t)gridDim.x * B);
 
@@ -103,20 +107,28 @@ __global__ void __launch_bounds__(kThreads)
     const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(first % B);
     unsigned long long cacc = 0;
-    float lacc = 0.0f;
-    bool bad = false;
+    LeafCounter<24> lsum;  // up to 2^24 - 1 leaves of 32 loss terms a thread
+    lsum.init();
+    float leaf = 0.0f;
+    int in_leaf = 0;
     for (long long it = first; it < total; it += stride) {
         const long long j = it / B;
         float f;
         bool sat;
-        clause_at(coff, lits, x, n, B, b, j, f, sat, bad);
+        clause_at(coff, lits, x, n, B, b, j, f, sat);
         if (!sat) {
             const long long wj = w ? __ldg(w + j) : 1ll;
             cacc += (unsigned long long)wj;
-            lacc += ((float)wj * f) * f;
+            const float term = ((float)wj * f) * f;
+            leaf = in_leaf == 0 ? term : leaf + term;
+            if (++in_leaf == 32) {
+                lsum.push(leaf);
+                in_leaf = 0;
+            }
         }
     }
-    if (bad) atomicOr(errflag, 1u);
+    if (in_leaf) lsum.push(leaf);
+    const float lacc = lsum.finish();
     s_c[threadIdx.x] = cacc;
     s_l[threadIdx.x] = lacc;
     __syncthreads();
@@ -203,7 +215,7 @@ extern "C" int msat_objective_noalloc(int32_t n_vars, int64_t n_clauses, const i
     int rc = scratch_address(&scratch);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 256, st);  // finish counter and error flag
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 256, st);  // finish counter
     if (e != cudaSuccess) return cuda_fail(e, "msat_objective_noalloc: clear counter");
     k_objective_noalloc<<<(unsigned)blocks, kThreads, 0, st>>>(
         clause_off, lits, weights, x, n_vars, n_clauses, B, static_cast<unsigned char *>(scratch),

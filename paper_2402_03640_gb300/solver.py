@@ -259,6 +259,9 @@ class Solver:
         loss = torch.empty(self.B, dtype=torch.float32, device=x.device)
         cost = torch.empty(self.B, dtype=torch.int64, device=x.device)
         check(self._lib.msat_forward(self._ctx, _p(x), _p(loss), _p(cost)))
+        # the context holds the state of one forward (tanh(x), the unsat
+        # mask, 2/N): count forwards so a backward can tell whose it is
+        self.probe_gen = getattr(self, "probe_gen", 0) + 1
         return loss, cost
 
     def backward(self, gscale=None):
@@ -370,11 +373,20 @@ def _make_autograd():
         def forward(ctx, x, solver):
             loss, _ = solver.forward(x)
             ctx.solver = solver
+            ctx.gen = solver.probe_gen
+            ctx.save_for_backward(x)
             return loss
 
         @staticmethod
         def backward(ctx, gout):
-            grad = ctx.solver.backward(gout)
+            solver = ctx.solver
+            if solver.probe_gen != ctx.gen:
+                # another forward ran on this solver since ours (for example
+                # two losses summed before one backward): the context holds
+                # its state, so evaluate this call's x again first
+                (x,) = ctx.saved_tensors
+                solver.forward(x)
+            grad = solver.backward(gout)
             return grad, None
 
     return MsatLoss

@@ -5,6 +5,8 @@ compared bit for bit with the oracle's FP32-canon mode (same seeds, same
 instances); losses and gradients within 1e-5 relative of the FP64 mode.
 Sizes span several thread blocks with ragged tails; the full-size
 configurations are checked on short trajectories."""
+import os
+
 import numpy as np
 import pytest
 
@@ -46,9 +48,9 @@ def gpu_trajectory(pkg, cnf, B, steps, lr, seed_x=1, chunk=1, per_pass=True, **k
                 best_cost=best, info=info)
 
 
-def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, per_pass=True, **kw):
+def check_bit_exact(oracle, cnf, B, steps, lr, chunk=1, seed_x=1, per_pass=True, oracle_threads=1, **kw):
     ref = oracle.solve(cnf, B, seed_x, steps, mode=oracle.MODE_F32, lr=lr,
-                       loss_norm=kw.get("loss_norm", "mean_unsat"))
+                       loss_norm=kw.get("loss_norm", "mean_unsat"), threads=oracle_threads)
     got = gpu_trajectory(pkg_module(), cnf, B, steps, lr, seed_x=seed_x, chunk=chunk,
                          per_pass=per_pass, **kw)
     idx = [0] + [min(k, steps) for k in range(chunk, steps + chunk, chunk)] if steps else [0]
@@ -181,12 +183,34 @@ def test_config2_weighted_zipf_full(pkg, oracle):
     check_bit_exact(oracle, cnf, 1, 6, 1e-4)
 
 
+_CORES = os.cpu_count() or 1
+
+
+@pytest.mark.slow
+def test_config1_batched_restarts_8_steps(pkg, oracle):
+    """Uniform 3-SAT n=5000, m=21500, B=256: 8 steps of cost history, x,
+    best cost and assignment bit for bit (the oracle's restarts split over
+    the host's cores)."""
+    cnf = uniform_ksat(5000, 21500, 3, seed=0)
+    check_bit_exact(oracle, cnf, 256, 8, 1e-4, oracle_threads=_CORES)
+
+
+@pytest.mark.slow
+def test_config2_weighted_zipf_500_steps(pkg, oracle):
+    """The weighted Zipf configuration for its full 500 steps: every int64
+    weighted cost of x_0 .. x_500, the final x, best cost and assignment."""
+    cnf = zipf_weighted(200000, 1000000, seed=0)
+    got, ref = check_bit_exact(oracle, cnf, 1, 500, 1e-4)
+    assert got["info"]["n_heavy"] > 0
+
+
 @pytest.mark.slow
 def test_config3_large_scale(pkg, oracle):
-    """Uniform 3-SAT n=1e6, m=4.3e6, B=16: one step from the seeded start
-    (the oracle needs seconds per step at this size)."""
+    """Uniform 3-SAT n=1e6, m=4.3e6, B=16: 5 steps from the seeded start,
+    every cost, x and best assignment bit for bit (the oracle's 16 restarts
+    run on the host's cores side by side)."""
     cnf = uniform_ksat(1000000, 4300000, 3, seed=0)
-    check_bit_exact(oracle, cnf, 16, 1, 1e-4)
+    check_bit_exact(oracle, cnf, 16, 5, 1e-4, oracle_threads=_CORES)
 
 
 # ------------------------------------------------------------ evaluate
@@ -229,6 +253,12 @@ def test_autograd_loss_and_gradient(pkg, oracle, weighted):
     assert np.allclose(lv, r64["loss"], rtol=1e-5, atol=0)
     tol = 1e-5 * np.abs(r64["grad"]).max(axis=0)
     assert np.all(np.abs(g.astype(np.float64) - r64["grad"]) <= tol[None, :])
+    # element-wise relative error where the gradient is not tiny against
+    # its restart's largest entry (there the scaled bound above governs)
+    sel = np.abs(r64["grad"]) > 1e-3 * np.abs(r64["grad"]).max(axis=0)[None, :]
+    assert sel.sum() > cnf.n * B // 2
+    rel = np.abs(g.astype(np.float64) - r64["grad"])[sel] / np.abs(r64["grad"])[sel]
+    assert rel.max() <= 1e-5
     assert np.array_equal(g, r32["grad"])
     # central differences of the FP64 objective at a few coordinates
     h = 1e-6
@@ -241,6 +271,25 @@ def test_autograd_loss_and_gradient(pkg, oracle, weighted):
         fd = (oracle.objective_f64(cnf, xp, want_grad=False)["loss"][b]
               - oracle.objective_f64(cnf, xm, want_grad=False)["loss"][b]) / (2 * h)
         assert abs(fd - g[i, b]) <= 1e-5 * np.abs(r64["grad"][:, b]).max() + 1e-9
+
+
+def test_autograd_two_forwards_before_backward(pkg, oracle):
+    """Two losses of one solver summed before a single backward: each
+    input gets the gradient of its own forward, although the context holds
+    the state of the latest forward only."""
+    import torch
+    cnf = uniform_ksat(300, 1290, 3, seed=8)
+    B = 4
+    xa, xb = oracle.init_x(cnf.n, B, 11), oracle.init_x(cnf.n, B, 12)
+    with pkg.Solver.from_cnf(cnf, restarts=B) as s:
+        ta = torch.from_numpy(xa).cuda().requires_grad_(True)
+        tb = torch.from_numpy(xb).cuda().requires_grad_(True)
+        la = pkg.msat_loss(ta, s)
+        lb = pkg.msat_loss(tb, s)
+        (la.sum() + 2.0 * lb.sum()).backward()
+        ga, gb = ta.grad.cpu().numpy(), tb.grad.cpu().numpy()
+    assert np.array_equal(ga, oracle.objective_f32(cnf, xa)["grad"])
+    assert np.array_equal(gb, oracle.objective_f32(cnf, xb)["grad"] * np.float32(2.0))
 
 
 def test_autograd_gradient_scaling(pkg, oracle):

@@ -461,3 +461,15 @@ def test_step32_matches_solve(oracle):
     assert np.array_equal(np.array(costs), ref["cost_hist"])
     assert np.array_equal(x.astype(np.float64), ref["x_final"])
     assert np.array_equal(best, ref["best_cost"])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_restart_split_equals_whole_run(oracle, mode):
+    """Restarts never interact: solving groups of restarts side by side
+    (each from its own first restart index) gives the arrays of one run."""
+    from synth import uniform_ksat, zipf_weighted
+    for cnf, B in ((uniform_ksat(60, 258, 3, seed=4), 7), (zipf_weighted(80, 300, seed=2), 5)):
+        whole = oracle.solve(cnf, B, 3, 25, mode=mode, lr=5e-2)
+        split = oracle.solve(cnf, B, 3, 25, mode=mode, lr=5e-2, threads=3)
+        for k in ("cost_hist", "loss_hist", "best_cost", "best_assign", "x_final"):
+            assert np.array_equal(whole[k], split[k]), k
