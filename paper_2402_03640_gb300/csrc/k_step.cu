@@ -1090,6 +1090,16 @@ __device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, c
         float leaf[VS];
 #pragma unroll
         for (int e = 0; e < VS; ++e) leaf[e] = 0.0f;
+        // occurrence words one batch ahead: the next batch's words are in
+        // flight while this batch's f values are gathered
+        int on[C];
+        int2 oxn[C];
+#pragma unroll
+        for (int u = 0; u < C; ++u) {
+            const bool okn = pb + u < pe;
+            on[u] = okn ? __ldcs(I.occ + pb + u) : 0;
+            oxn[u] = (expanded && okn) ? __ldcs(I.occx + pb + u) : make_int2(0, 0);
+        }
         for (int p = pb; p < pe; p += C) {
             int o[C];
             int2 ox[C];
@@ -1097,8 +1107,11 @@ __device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, c
 #pragma unroll
             for (int u = 0; u < C; ++u) {
                 ok[u] = p + u < pe;
-                o[u] = ok[u] ? __ldcs(I.occ + p + u) : 0;
-                ox[u] = (expanded && ok[u]) ? __ldcs(I.occx + p + u) : make_int2(0, 0);
+                o[u] = on[u];
+                ox[u] = oxn[u];
+                const bool okn = p + C + u < pe;
+                on[u] = okn ? __ldcs(I.occ + p + C + u) : 0;
+                oxn[u] = (expanded && okn) ? __ldcs(I.occx + p + C + u) : make_int2(0, 0);
             }
             occ_accumulate<VS, KFIX, C, STORE>(I, S, kfix, tcur, o, ox, ok, i, col, cs, dense, p == pb, leaf);
         }
