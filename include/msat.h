@@ -253,13 +253,14 @@ int msat_check(msat_ctx *ctx);
 /*
  * Failure-detection self-test (no counterpart in the paper).  Every device
  * wait of this library (the mbarrier phases of the tensor-core evaluator)
- * gives up after a bounded number of tries, records the reason in an error
- * flag and returns, so a phase that never completes is reported by
- * msat_check as MSAT_ETIMEOUT instead of hanging the GPU.  This call runs
- * that path on purpose: one thread waits `spins` tries (1 .. 2^24) on a
- * barrier nothing arrives at.  Returns MSAT_ETIMEOUT (the expected result)
- * with the flag in the message; the device stays usable.  Synchronous;
- * allocates and frees one 4-byte flag.
+ * gives up after 200 ms of the GPU's global timer (a phase normally
+ * completes within microseconds), records the reason in an error flag and
+ * returns, so a phase that never completes is reported by msat_check as
+ * MSAT_ETIMEOUT instead of hanging the GPU.  This call runs that path on
+ * purpose: one thread waits on a barrier nothing arrives at, for `spins`
+ * tries (1 .. 2^24) or, with spins = 0, until the 200 ms limit.  Returns
+ * MSAT_ETIMEOUT (the expected result) with the flag in the message; the
+ * device stays usable.  Synchronous; allocates and frees one 4-byte flag.
  */
 int msat_selftest_bounded_wait(int64_t spins);
 

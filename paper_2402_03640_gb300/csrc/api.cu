@@ -1024,8 +1024,8 @@ extern "C" int msat_backward(msat_ctx *c, const float *gscale, float *grad) {
 }
 
 extern "C" int msat_selftest_bounded_wait(int64_t spins) {
-    if (spins < 1 || spins > (1LL << 24))
-        return fail(MSAT_EINVAL, "msat_selftest_bounded_wait: spins must be in [1, 2^24]");
+    if (spins < 0 || spins > (1LL << 24))
+        return fail(MSAT_EINVAL, "msat_selftest_bounded_wait: spins must be in [0, 2^24]");
     unsigned int *flag = nullptr;
     cudaError_t e = cudaMalloc(&flag, sizeof(unsigned));
     if (e) return cuda_fail(e, "msat_selftest_bounded_wait: allocation");
@@ -1035,8 +1035,10 @@ extern "C" int msat_selftest_bounded_wait(int64_t spins) {
     if (!e) e = cudaMemcpy(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost);
     cudaFree(flag);
     if (e) return cuda_fail(e, "msat_selftest_bounded_wait");
-    if (h) return fail(MSAT_ETIMEOUT, "msat_selftest_bounded_wait: the wait gave up after " +
-                                          std::to_string(spins) + " tries (flag " + std::to_string(h) + ")");
+    if (h)
+        return fail(MSAT_ETIMEOUT, "msat_selftest_bounded_wait: the wait gave up after " +
+                                       (spins ? std::to_string(spins) + " tries" : std::string("its time limit")) +
+                                       " (flag " + std::to_string(h) + ")");
     return MSAT_OK;
 }
 

@@ -33,8 +33,14 @@
 // k-range.  A piece therefore tests its own partial sums against those
 // per-piece targets, stores one bit per (clause, assignment) and counts
 // itself in; the last piece of a tile to arrive ANDs the other pieces' bits
-// into its own and counts the unsat clauses.  No CTA waits on another.  Every mbarrier wait is bounded: on a timeout the block records
-// an error flag, stops issuing work and still frees its TMEM.
+// into its own and counts the unsat clauses.  No CTA waits on another.
+//
+// Every mbarrier wait gives up after kWaitNs nanoseconds of %globaltimer
+// (200 ms; a phase normally completes within microseconds).  On a timeout
+// the block records an error flag and stops issuing work; the MMA issuer
+// then waits (bounded) until the MMAs it has issued have completed, the
+// producer until the copies it has issued have landed, and only then does
+// the block free its TMEM.
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -56,7 +62,7 @@ constexpr int kAccBufs = 2;         // TMEM accumulators (segment j uses j % 2)
 constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
-constexpr long long kSpin = 1LL << 26;
+constexpr unsigned long long kWaitNs = 200ull * 1000ull * 1000ull;  // 200 ms
 // e2m1 codes (sign, 2 exponent bits with bias 1, 1 mantissa bit)
 constexpr uint8_t kE2M1One = 0x2, kE2M1MinusOne = 0xA;
 
@@ -69,6 +75,7 @@ struct DenseHeader {
     int abort;
     int epi_fail;  // written only by the epilogue warps, read after their barrier
     int last;      // this CTA finishes the split tile
+    unsigned long long drain;  // the MMA issuer's last MMAs completed (abort path)
     unsigned long long colsum[256];
 };
 static_assert(sizeof(DenseHeader) <= kHeader, "dense header does not fit");
@@ -98,21 +105,32 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
     return ok != 0;
 }
 
-// Bounded wait on a barrier phase; false after kSpin tries.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long limit) {
-    for (long long i = 0; i < limit; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on a barrier phase: false once max_ns nanoseconds of the
+// global timer have passed (or after max_tries tries, when max_tries > 0).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long max_tries,
+                                          unsigned long long max_ns) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0; max_tries <= 0 || i < max_tries; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > max_ns) return false;
+    }
     return false;
 }
 
-// The same, giving up early once another role of the block has aborted.
-__device__ __forceinline__ bool mbar_wait_abort(unsigned long long *bar, uint32_t parity, long long limit,
-                                                const int *abort) {
-    for (long long i = 0; i < limit; ++i) {
+// The same with the kernel's time limit, giving up early once another
+// role of the block has aborted.
+__device__ __forceinline__ bool mbar_wait_abort(unsigned long long *bar, uint32_t parity, const int *abort) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023) == 1023 && *(volatile const int *)abort) return false;
+        if ((i & 255) == 255 && (*(volatile const int *)abort || global_ns() - t0 > kWaitNs)) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
@@ -249,6 +267,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             mbar_init(&H->acc_full[b], 1);
             mbar_init(&H->acc_empty[b], 4);  // one arrive per epilogue warp
         }
+        mbar_init(&H->drain, 1);
         H->abort = 0;
         H->epi_fail = 0;
         H->last = 0;
@@ -283,7 +302,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
                 if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kTK, m0);
                 if (it >= kStages) {
                     const uint32_t parity = (uint32_t)((it / kStages - 1) & 1);
-                    if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, kSpin)) {
+                    if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, 0, kWaitNs)) {
                         H->abort = 1;
                         atomicOr(errflag, 1u);
                         stop = true;
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         }
         // every issued copy has landed before the block may exit
         for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
-            if (!mbar_wait(&H->full[i % kStages], (uint32_t)((i / kStages) & 1), kSpin)) atomicOr(errflag, 2u);
+            if (!mbar_wait(&H->full[i % kStages], (uint32_t)((i / kStages) & 1), 0, kWaitNs)) atomicOr(errflag, 2u);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: segment j accumulates into TMEM buffer j % 2 once the
         // epilogue has read what the segment before last left there
@@ -312,16 +331,17 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             const DenseSeg g = seg_at(d, cta, j);
             const int buf = j % kAccBufs;
             if (j >= kAccBufs &&
-                !mbar_wait_abort(&H->acc_empty[buf], (uint32_t)((j / kAccBufs - 1) & 1), 4 * kSpin, &H->abort)) {
+                !mbar_wait_abort(&H->acc_empty[buf], (uint32_t)((j / kAccBufs - 1) & 1), &H->abort)) {
                 H->abort = 1;
                 atomicOr(errflag, 1u);
+                stop = true;
                 break;
             }
             tc_fence_after();
             const uint32_t acc = tmem + (uint32_t)(buf * tmem_cols);
             for (int kt = g.ka; kt < g.kb; ++kt) {
                 const int s = it % kStages;
-                if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((it / kStages) & 1), kSpin)) {
+                if (*(volatile int *)&H->abort || !mbar_wait(&H->full[s], (uint32_t)((it / kStages) & 1), 0, kWaitNs)) {
                     H->abort = 1;
                     atomicOr(errflag, 1u);
                     stop = true;
@@ -340,6 +360,13 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             if (stop) break;
             mma_commit(&H->acc_full[buf]);  // arrives once every MMA of the segment has completed
         }
+        if (stop) {
+            // MMAs issued before the abort may still be writing TMEM: wait
+            // (bounded) until all of them have completed before the block
+            // reaches the barrier that precedes the TMEM release
+            mma_commit(&H->drain);
+            if (!mbar_wait(&H->drain, 0u, 0, kWaitNs)) atomicOr(errflag, 16u);
+        }
     } else if (warp >= 2) {
         // epilogue: TMEM lane quarter q (= warp % 4) holds clause rows
         // m0 + 32q .. + 31 of the segment's tile
@@ -349,7 +376,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         for (int j = 0; j < nseg; ++j) {
             const DenseSeg g = seg_at(d, cta, j);
             const int buf = j % kAccBufs;
-            const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / kAccBufs) & 1), 4 * kSpin, &H->abort);
+            const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / kAccBufs) & 1), &H->abort);
             if (!ok) H->epi_fail = 1;
             epi_sync();
             if (H->epi_fail) {  // the same decision in all four warps
@@ -450,15 +477,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier that
-// nothing arrives at, gives up after `spins` tries and records it in the
-// error flag -- the path every wait of k_dense_eval takes when a phase never
-// completes.  Nothing faults and nothing hangs; the context stays usable.
+// nothing arrives at, gives up after `spins` tries (spins = 0: on the
+// kernels' own time limit, kWaitNs) and records it in the error flag --
+// the path every wait of k_dense_eval takes when a phase never completes.
+// Nothing faults and nothing hangs; the context stays usable.
 __global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
     __shared__ unsigned long long bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (!mbar_wait(&bar, 0u, spins)) atomicOr(errflag, 8u);
+        if (!mbar_wait(&bar, 0u, spins, kWaitNs)) atomicOr(errflag, 8u);
     }
 }
 

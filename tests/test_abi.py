@@ -99,7 +99,8 @@ def test_null_arguments(lib):
     assert lib.msat_solve(None, 1, 1.0, 1, None, None, None, None, 0, None) == native.MSAT_EINVAL
     assert lib.msat_step_ex(None, 1, 0, None, None) == native.MSAT_EINVAL
     assert lib.msat_heuristic_gap(None, None, None) == native.MSAT_EINVAL
-    assert lib.msat_selftest_bounded_wait(0) == native.MSAT_EINVAL
+    assert lib.msat_selftest_bounded_wait(-1) == native.MSAT_EINVAL
+    assert lib.msat_selftest_bounded_wait((1 << 24) + 1) == native.MSAT_EINVAL
     assert lib.msat_best_step(None, None) == native.MSAT_EINVAL
     assert lib.msat_autotune(1, 0, None, None, None, None, None, 1, None, None, 0, None) == native.MSAT_EINVAL
     lib.msat_destroy(None)

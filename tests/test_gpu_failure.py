@@ -29,6 +29,13 @@ def test_bounded_wait_times_out_and_device_stays_usable(pkg, oracle):
         rc = lib.msat_selftest_bounded_wait(spins)
         assert rc == native.MSAT_ETIMEOUT
         assert b"gave up" in lib.msat_last_error()
+    # spins = 0: the kernels' own limit, 200 ms of the GPU's global timer
+    import time
+    t = time.perf_counter()
+    rc = lib.msat_selftest_bounded_wait(0)
+    dt = time.perf_counter() - t
+    assert rc == native.MSAT_ETIMEOUT and b"time limit" in lib.msat_last_error()
+    assert 0.15 < dt < 5.0
     # the context and the kernels still work afterwards
     cnf = uniform_ksat(50, 215, 3, seed=0)
     ref = oracle.solve(cnf, 2, 1, 40, mode=oracle.MODE_F32, lr=1e-2, want_hist=False)
