@@ -1097,8 +1097,8 @@ __device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, c
 #pragma unroll
         for (int u = 0; u < C; ++u) {
             const bool okn = pb + u < pe;
-            on[u] = okn ? __ldcs(I.occ + pb + u) : 0;
-            oxn[u] = (expanded && okn) ? __ldcs(I.occx + pb + u) : make_int2(0, 0);
+            on[u] = okn ? __ldg(I.occ + pb + u) : 0;
+            oxn[u] = (expanded && okn) ? __ldg(I.occx + pb + u) : make_int2(0, 0);
         }
         for (int p = pb; p < pe; p += C) {
             int o[C];
@@ -1110,8 +1110,8 @@ __device__ __forceinline__ void vars_body(const DevInst &I, const DevState &S, c
                 o[u] = on[u];
                 ox[u] = oxn[u];
                 const bool okn = p + C + u < pe;
-                on[u] = okn ? __ldcs(I.occ + p + C + u) : 0;
-                oxn[u] = (expanded && okn) ? __ldcs(I.occx + p + C + u) : make_int2(0, 0);
+                on[u] = okn ? __ldg(I.occ + p + C + u) : 0;
+                oxn[u] = (expanded && okn) ? __ldg(I.occx + p + C + u) : make_int2(0, 0);
             }
             occ_accumulate<VS, KFIX, C, STORE>(I, S, kfix, tcur, o, ox, ok, i, col, cs, dense, p == pb, leaf);
         }
