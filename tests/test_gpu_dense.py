@@ -97,3 +97,13 @@ def test_evaluate_current_x_both_backends(pkg, oracle):
         s.check()
     assert np.array_equal(cost, ref["cost_hist"][-1])
     assert np.array_equal(d, cost) and np.array_equal(sp, cost)
+
+
+@pytest.mark.parametrize("m,nbs", [(19500, [64, 256]), (25000, [16, 200]), (40000, [300])])
+def test_dense_tile_counts_past_one_wave(pkg, oracle, m, nbs):
+    """Clause-tile counts just above one wave of SMs (a small leftover split
+    into k-step pieces), between one and two waves and above two (whole
+    tiles in a last partial wave; two assignment tiles for 300
+    assignments)."""
+    cnf = uniform_ksat(3000, m, 3, seed=m)
+    _check(pkg, oracle, cnf, nbs, seed=m)
