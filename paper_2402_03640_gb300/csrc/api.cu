@@ -35,6 +35,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 using namespace msat;
 
 #include "ctx.cuh"
+#include "host_cnf.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -159,75 +160,16 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
         !(cfg.eps >= 0))
         return fail(MSAT_EINVAL, "msat_create: Adam settings out of range");
     const int64_t m = n_clauses;
-    if (clause_off[0] != 0) return fail(MSAT_EINVAL, "msat_create: clause_off[0] must be 0");
-    for (int64_t j = 0; j < m; ++j)
-        if (clause_off[j + 1] < clause_off[j])
-            return fail(MSAT_EINVAL, "msat_create: clause_off is not non-decreasing at clause " +
-                                         std::to_string(j));
-    const int64_t raw = clause_off[m];
-    if (raw > 0 && !lits) return fail(MSAT_EINVAL, "msat_create: lits is NULL");
-    if (raw >= (1LL << 31)) return fail(MSAT_EINVAL, "msat_create: more than 2^31-1 literals");
-    for (int64_t q = 0; q < raw; ++q) {
-        const int32_t l = lits[q];
-        if (l == 0 || l > n_vars || l < -n_vars)
-            return fail(MSAT_EINVAL, "msat_create: literal " + std::to_string(l) + " at position " +
-                                         std::to_string(q) + " is 0 or names no variable");
-    }
-    if (weights)
-        for (int64_t j = 0; j < m; ++j)
-            if (weights[j] < 1)
-                return fail(MSAT_EINVAL, "msat_create: weight of clause " + std::to_string(j) +
-                                             " is below 1");
-
-    // canonical clauses: drop a literal equal to an earlier one of its clause
-    // (the first occurrence keeps its place); seen[literal] is the last
-    // clause that kept it, so a clause costs O(its length)
-    std::vector<int32_t> coff((size_t)m + 1);
-    std::vector<int32_t> lit;
-    lit.reserve((size_t)raw);
-    std::vector<int32_t> seen((size_t)n_vars * 2, -1);
-    int64_t wsum = 0;
-    int32_t max_len = 0;
-    coff[0] = 0;
-    for (int64_t j = 0; j < m; ++j) {
-        const size_t start = lit.size();
-        for (int64_t p = clause_off[j]; p < clause_off[j + 1]; ++p) {
-            const int32_t l = lits[p];
-            const int32_t packed = ((std::abs(l) - 1) << 1) | (l < 0 ? 1 : 0);
-            if (seen[(size_t)packed] == (int32_t)j) continue;
-            seen[(size_t)packed] = (int32_t)j;
-            lit.push_back(packed);
-        }
-        const int32_t len = (int32_t)(lit.size() - start);
-        if (len > kMaxClauseLen)
-            return fail(MSAT_EINVAL, "msat_create: clause " + std::to_string(j) + " has " +
-                                         std::to_string(len) + " literals (limit 1024)");
-        max_len = std::max(max_len, len);
-        coff[(size_t)j + 1] = (int32_t)lit.size();
-        wsum += weights ? weights[j] : 1;
-    }
-    const int64_t nnz = (int64_t)lit.size();
-    int32_t kfix = 0;
-    if (m > 0) {
-        kfix = coff[1] - coff[0];
-        for (int64_t j = 1; j < m && kfix > 0; ++j)
-            if (coff[(size_t)j + 1] - coff[(size_t)j] != kfix) kfix = 0;
-    }
-    // transposed CSR: occurrences of each variable in (clause, position) order
-    std::vector<int32_t> voff((size_t)n_vars + 1, 0);
-    for (int32_t L : lit) voff[(size_t)(L >> 1) + 1] += 1;
-    for (int32_t i = 0; i < n_vars; ++i) voff[(size_t)i + 1] += voff[(size_t)i];
-    std::vector<int32_t> occ((size_t)nnz);
+    // checks, canonical clauses and the transposed CSR (host_cnf.cu, on the
+    // host's cores)
+    HostCnf hc;
     {
-        std::vector<int32_t> fill(voff.begin(), voff.end() - 1);
-        for (int64_t j = 0; j < m; ++j)
-            for (int32_t p = coff[(size_t)j]; p < coff[(size_t)j + 1]; ++p) {
-                const int32_t L = lit[(size_t)p];
-                occ[(size_t)fill[(size_t)(L >> 1)]++] = (int32_t)(j << 1) | (L & 1);
-            }
+        const int hrc = build_host_cnf(n_vars, m, clause_off, lits, weights, hc);
+        if (hrc) return hrc;
     }
-    int32_t max_deg = 0;
-    for (int32_t i = 0; i < n_vars; ++i) max_deg = std::max(max_deg, voff[(size_t)i + 1] - voff[(size_t)i]);
+    I32Buf &coff = hc.coff, &lit = hc.lit, &voff = hc.voff, &occ = hc.occ;
+    const int64_t nnz = hc.nnz, wsum = hc.wsum;
+    const int32_t max_len = hc.max_len, kfix = hc.kfix, max_deg = hc.max_deg;
     if ((int64_t)max_deg > 4095LL * 32 * kChunk)
         return fail(MSAT_EINVAL, "msat_create: a variable occurs more than 4095*32768 times");
     const int32_t B = cfg.restarts;
@@ -329,22 +271,8 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     c->max_len = max_len;
     c->max_deg = max_deg;
     c->wsum = wsum;
-    c->clen.resize((size_t)m);
-    c->taut.assign((size_t)m, 0);
-    {
-        // after the repeats are gone, a variable seen twice in a clause
-        // appears as x and not x: the clause can never be unsat
-        std::vector<int32_t> vseen((size_t)n_vars, -1);
-        for (int64_t j = 0; j < m; ++j) {
-            const int32_t b0 = coff[(size_t)j], b1 = coff[(size_t)j + 1];
-            c->clen[(size_t)j] = b1 - b0;
-            for (int32_t p = b0; p < b1; ++p) {
-                const int32_t v = lit[(size_t)p] >> 1;
-                if (vseen[(size_t)v] == (int32_t)j) c->taut[(size_t)j] = 1;
-                vseen[(size_t)v] = (int32_t)j;
-            }
-        }
-    }
+    c->clen = std::move(hc.clen);
+    c->taut = std::move(hc.taut);
     if (weights) c->wts.assign(weights, weights + m);
 
     const int64_t nB = (int64_t)n_vars * B;

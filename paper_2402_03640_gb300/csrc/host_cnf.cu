@@ -1,0 +1,234 @@
+// Host side of msat_create: check the caller's CNF, make its clauses
+// canonical and build the transposed CSR, spread over the host's cores.
+//
+// The result is the one a single thread produces, bit for bit: clauses keep
+// their order and their literals the order of their first occurrence; the
+// occurrence list of each variable is in (clause, position) order.  Each
+// thread takes a contiguous range of clauses (or literals), and the
+// per-thread pieces are joined in range order; every reported error is the
+// first one in input order, as a sequential scan would find it.
+
+#include <stdint.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "msat_internal.cuh"
+#include "host_cnf.cuh"
+
+namespace msat {
+
+namespace {
+
+// Runs f(t, begin, end) on T threads over [0, N) in T contiguous ranges.
+template <class F>
+void parallel_ranges(int64_t N, int T, F f) {
+    if (T <= 1 || N < 2) {
+        f(0, (int64_t)0, N);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)T);
+    for (int t = 0; t < T; ++t) {
+        const int64_t b = N * t / T, e = N * (t + 1) / T;
+        th.emplace_back([=, &f] { f(t, b, e); });
+    }
+    for (auto &x : th) x.join();
+}
+
+int threads_for(int64_t work) {
+    unsigned hc = std::thread::hardware_concurrency();
+    if (hc == 0) hc = 1;
+    int64_t t = std::min<int64_t>((int64_t)hc, 32);
+    t = std::min<int64_t>(t, std::max<int64_t>(1, work / (1 << 16)));
+    return (int)t;
+}
+
+}  // namespace
+
+int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
+                   HostCnf &out) {
+    if (off[0] != 0) return fail(MSAT_EINVAL, "msat_create: clause_off[0] must be 0");
+    const int Tm = threads_for(m);
+    {
+        std::vector<int64_t> bad((size_t)Tm, -1);
+        parallel_ranges(m, Tm, [&](int t, int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; ++j)
+                if (off[j + 1] < off[j]) {
+                    bad[(size_t)t] = j;
+                    return;
+                }
+        });
+        for (int64_t j : bad)
+            if (j >= 0)
+                return fail(MSAT_EINVAL, "msat_create: clause_off is not non-decreasing at clause " +
+                                             std::to_string(j));
+    }
+    const int64_t raw = off[m];
+    if (raw > 0 && !lits) return fail(MSAT_EINVAL, "msat_create: lits is NULL");
+    if (raw >= (1LL << 31)) return fail(MSAT_EINVAL, "msat_create: more than 2^31-1 literals");
+    {
+        const int Tq = threads_for(raw);
+        std::vector<int64_t> bad((size_t)Tq, -1);
+        parallel_ranges(raw, Tq, [&](int t, int64_t b, int64_t e) {
+            for (int64_t q = b; q < e; ++q) {
+                const int32_t l = lits[q];
+                if (l == 0 || l > n || l < -n) {
+                    bad[(size_t)t] = q;
+                    return;
+                }
+            }
+        });
+        for (int64_t q : bad)
+            if (q >= 0)
+                return fail(MSAT_EINVAL, "msat_create: literal " + std::to_string(lits[q]) + " at position " +
+                                             std::to_string(q) + " is 0 or names no variable");
+    }
+    if (w) {
+        std::vector<int64_t> bad((size_t)Tm, -1);
+        parallel_ranges(m, Tm, [&](int t, int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; ++j)
+                if (w[j] < 1) {
+                    bad[(size_t)t] = j;
+                    return;
+                }
+        });
+        for (int64_t j : bad)
+            if (j >= 0)
+                return fail(MSAT_EINVAL, "msat_create: weight of clause " + std::to_string(j) + " is below 1");
+    }
+
+    // canonical clauses: drop a literal equal to an earlier one of its clause
+    // (the first occurrence keeps its place); after that a variable seen
+    // twice in a clause appears as x and not x, and the clause can never be
+    // unsat.  Short clauses compare pairwise; a long one marks literals and
+    // variables in the thread's own arrays (marked with the clause index).
+    struct Part {
+        std::vector<int32_t> lit;
+        int64_t wsum = 0;
+        int32_t max_len = 0;
+        int64_t too_long = -1;
+        std::vector<int32_t> seen, vseen;
+    };
+    std::vector<Part> parts((size_t)Tm);
+    out.clen.assign((size_t)m, 0);
+    out.taut.assign((size_t)m, 0);
+    parallel_ranges(m, Tm, [&](int t, int64_t b, int64_t e) {
+        Part &P = parts[(size_t)t];
+        P.lit.reserve((size_t)(off[e] - off[b]));
+        for (int64_t j = b; j < e; ++j) {
+            const size_t start = P.lit.size();
+            const int64_t len_in = off[j + 1] - off[j];
+            bool taut = false;
+            if (len_in <= 32) {
+                for (int64_t p = off[j]; p < off[j + 1]; ++p) {
+                    const int32_t l = lits[p];
+                    const int32_t packed = ((std::abs(l) - 1) << 1) | (l < 0 ? 1 : 0);
+                    bool dup = false;
+                    for (size_t r = start; r < P.lit.size(); ++r) {
+                        if (P.lit[r] == packed) dup = true;
+                        else if ((P.lit[r] >> 1) == (packed >> 1)) taut = true;
+                    }
+                    if (!dup) P.lit.push_back(packed);
+                }
+            } else {
+                if (P.seen.empty()) {
+                    P.seen.assign((size_t)n * 2, -1);
+                    P.vseen.assign((size_t)n, -1);
+                }
+                for (int64_t p = off[j]; p < off[j + 1]; ++p) {
+                    const int32_t l = lits[p];
+                    const int32_t packed = ((std::abs(l) - 1) << 1) | (l < 0 ? 1 : 0);
+                    if (P.seen[(size_t)packed] == (int32_t)j) continue;
+                    P.seen[(size_t)packed] = (int32_t)j;
+                    P.lit.push_back(packed);
+                    if (P.vseen[(size_t)(packed >> 1)] == (int32_t)j) taut = true;
+                    P.vseen[(size_t)(packed >> 1)] = (int32_t)j;
+                }
+            }
+            const int32_t len = (int32_t)(P.lit.size() - start);
+            if (len > kMaxClauseLen && P.too_long < 0) P.too_long = j;
+            P.max_len = std::max(P.max_len, len);
+            out.clen[(size_t)j] = len;
+            out.taut[(size_t)j] = taut ? 1 : 0;
+            P.wsum += w ? w[j] : 1;
+        }
+    });
+    for (const Part &P : parts)
+        if (P.too_long >= 0)
+            return fail(MSAT_EINVAL, "msat_create: clause " + std::to_string(P.too_long) + " has " +
+                                         std::to_string(out.clen[(size_t)P.too_long]) +
+                                         " literals (limit 1024)");
+    // join the parts in clause order
+    std::vector<int64_t> lbase((size_t)Tm + 1, 0);
+    out.wsum = 0;
+    out.max_len = 0;
+    for (int t = 0; t < Tm; ++t) {
+        lbase[(size_t)t + 1] = lbase[(size_t)t] + (int64_t)parts[(size_t)t].lit.size();
+        out.wsum += parts[(size_t)t].wsum;
+        out.max_len = std::max(out.max_len, parts[(size_t)t].max_len);
+    }
+    out.nnz = lbase[(size_t)Tm];
+    out.lit.alloc((size_t)out.nnz);
+    out.coff.alloc((size_t)m + 1);
+    out.coff[0] = 0;
+    parallel_ranges(m, Tm, [&](int t, int64_t b, int64_t e) {
+        const Part &P = parts[(size_t)t];
+        std::copy(P.lit.begin(), P.lit.end(), out.lit.data() + lbase[(size_t)t]);
+        int64_t at = lbase[(size_t)t];
+        for (int64_t j = b; j < e; ++j) {
+            at += out.clen[(size_t)j];
+            out.coff[(size_t)j + 1] = (int32_t)at;
+        }
+    });
+    parts.clear();
+    out.kfix = 0;
+    if (m > 0) {
+        out.kfix = out.clen[0];
+        for (int64_t j = 1; j < m && out.kfix > 0; ++j)
+            if (out.clen[(size_t)j] != out.kfix) out.kfix = 0;
+    }
+
+    // transposed CSR, stable: per-thread counts of each variable's
+    // occurrences in the thread's clause range, turned into per-thread
+    // write positions (earlier ranges first), then one scatter pass
+    int Tt = threads_for(out.nnz);
+    while (Tt > 1 && (int64_t)Tt * n > (int64_t)64 << 20) --Tt;  // counts within 256 MB
+    std::unique_ptr<int32_t[]> cnt(new int32_t[(size_t)Tt * n]);
+    parallel_ranges(m, Tt, [&](int t, int64_t b, int64_t e) {
+        int32_t *c = cnt.get() + (size_t)t * n;
+        std::fill(c, c + n, 0);
+        for (int64_t p = out.coff[(size_t)b]; p < out.coff[(size_t)e]; ++p) ++c[out.lit[(size_t)p] >> 1];
+    });
+    out.voff.alloc((size_t)n + 1);
+    int64_t acc = 0;
+    out.max_deg = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        out.voff[(size_t)i] = (int32_t)acc;
+        int64_t d = 0;
+        for (int t = 0; t < Tt; ++t) {
+            int32_t &c = cnt[(size_t)t * n + i];
+            const int32_t k = c;
+            c = (int32_t)(acc + d);  // thread t's first slot for variable i
+            d += k;
+        }
+        acc += d;
+        out.max_deg = std::max<int32_t>(out.max_deg, (int32_t)d);
+    }
+    out.voff[(size_t)n] = (int32_t)acc;
+    out.occ.alloc((size_t)out.nnz);
+    parallel_ranges(m, Tt, [&](int t, int64_t b, int64_t e) {
+        int32_t *c = cnt.get() + (size_t)t * n;
+        for (int64_t j = b; j < e; ++j)
+            for (int32_t p = out.coff[(size_t)j]; p < out.coff[(size_t)j + 1]; ++p) {
+                const int32_t L = out.lit[(size_t)p];
+                out.occ[(size_t)c[L >> 1]++] = (int32_t)(j << 1) | (L & 1);
+            }
+    });
+    return MSAT_OK;
+}
+
+}  // namespace msat
