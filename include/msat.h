@@ -124,7 +124,7 @@ int msat_config_default(msat_config *cfg);
  * A literal repeated inside a clause is dropped (W has one entry per
  * variable and clause); a clause holding x and not x is kept and is never
  * unsatisfied; an empty clause is always unsatisfied.  Clauses longer than
- * 1024 literals, nnz >= 2^31 and m or n >= 2^30 are rejected (MSAT_EINVAL).
+ * 32767 literals, nnz >= 2^31 and m or n >= 2^30 are rejected (MSAT_EINVAL).
  * x is initialised on the device: x[i][b] = k * 2^-23 - 1 with k the top 24
  * bits of output number b*n + i of the SplitMix64 stream seeded with
  * seed_x; Adam moments are zero; the best cost starts at sum_j w_j.

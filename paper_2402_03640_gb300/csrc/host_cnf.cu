@@ -161,7 +161,7 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
         if (P.too_long >= 0)
             return fail(MSAT_EINVAL, "msat_create: clause " + std::to_string(P.too_long) + " has " +
                                          std::to_string(out.clen[(size_t)P.too_long]) +
-                                         " literals (limit 1024)");
+                                         " literals (limit " + std::to_string(kMaxClauseLen) + ")");
     // join the parts in clause order
     std::vector<int64_t> lbase((size_t)Tm + 1, 0);
     out.wsum = 0;

@@ -103,7 +103,7 @@ __global__ void k_heuristic_gap(DevInst I, const float *__restrict__ x,
             beg = __ldg(I.coff + j);
             end = __ldg(I.coff + j + 1);
         }
-        LeafCounter<6> lc;
+        LeafCounter<kClauseLevels> lc;
         lc.init();
         float leaf = 0.0f;
         int in_leaf = 0;

@@ -133,7 +133,7 @@ __device__ __forceinline__ void clause_range(const DevInst &I, int kfix, int j, 
 // indexed at run time: it lives in local memory and is touched once per 32
 // literals, so short clauses never use it.
 template <int VW>
-__device__ __forceinline__ void leaf_push(float (&stk)[6][VW], unsigned &cnt, float (&v)[VW]) {
+__device__ __forceinline__ void leaf_push(float (&stk)[kClauseLevels][VW], unsigned &cnt, float (&v)[VW]) {
     unsigned c = cnt;
     int lvl = 0;
     while (c & 1u) {
@@ -148,9 +148,9 @@ __device__ __forceinline__ void leaf_push(float (&stk)[6][VW], unsigned &cnt, fl
 }
 
 template <int VW>
-__device__ __forceinline__ void leaf_finish(const float (&stk)[6][VW], unsigned cnt, float (&r)[VW]) {
+__device__ __forceinline__ void leaf_finish(const float (&stk)[kClauseLevels][VW], unsigned cnt, float (&r)[VW]) {
     bool have = false;
-    for (int lvl = 0; lvl < 6; ++lvl) {
+    for (int lvl = 0; lvl < kClauseLevels; ++lvl) {
         if (!((cnt >> lvl) & 1u)) continue;
 #pragma unroll
         for (int e = 0; e < VW; ++e) r[e] = have ? (stk[lvl][e] + r[e]) : stk[lvl][e];
@@ -170,7 +170,7 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
         f[e] = 0.0f;
         sat[e] = false;
     }
-    float stk[6][VW];
+    float stk[kClauseLevels][VW];
     unsigned nleaf = 0;
     int in_leaf = 0;
 #pragma unroll 2
@@ -1342,7 +1342,7 @@ __device__ __forceinline__ float small_clause_f(const DevInst &I, const float *_
     const int B = I.B;
     int beg, end;
     clause_range(I, I.kfix, j, beg, end);
-    LeafCounter<6> lc;
+    LeafCounter<kClauseLevels> lc;
     lc.init();
     float leaf = 0.0f;
     int in_leaf = 0;

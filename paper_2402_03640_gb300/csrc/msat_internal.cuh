@@ -152,7 +152,8 @@ constexpr int kThreads = 256;
 constexpr int kRep = 32;                 // replicas of the per-restart cost accumulator
 constexpr int kTaskCap = 256;          // default leaf tasks of one light block
 constexpr int kLightMaxDeg = 512;      // more occurrences than this: heavy variable
-constexpr int kMaxClauseLen = 1024;  // 32 leaves -> 5 levels of the leaf counter
+constexpr int kMaxClauseLen = 32767;  // at most 1024 leaves of 32 literals
+constexpr int kClauseLevels = 11;     // binary leaf counter of a clause sum (1024 leaves)
 constexpr int kChunk = 1024;         // occurrences per heavy-variable chunk (32 leaves)
 
 // Shared memory of a light block: the partial sums of its leaf tasks

@@ -79,7 +79,7 @@ def _create(lib, n, off, lits, w=None, restarts=1, **shape):
     (dict(n=2, off=[0, 2], lits=[1, 2], w=[0]), "weight"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=3), "power of two"),
     (dict(n=0, off=[0], lits=[1]), "n_vars"),
-    (dict(n=2000, off=[0, 1030], lits=list(range(1, 1031))), "limit 1024"),
+    (dict(n=40000, off=[0, 32768], lits=list(range(1, 32769))), "limit 32767"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=1024, fwd_vw=2), "must not exceed 256"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=512, stage_vw=1), "must not exceed 256"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=4, fwd_vw=8), "powers of two"),

@@ -154,6 +154,26 @@ def test_long_clauses_and_mixed_lengths(pkg, oracle):
     check_bit_exact(oracle, cnf, 2, 15, 5e-2)
 
 
+def test_clauses_of_thousands_of_literals(pkg, oracle):
+    """Clauses of 20000 and 5000 literals (hundreds of 32-literal leaves in
+    the dyadic counter) among 3-literal clauses: trajectories bit for bit,
+    and the tensor-core evaluation of the result."""
+    rng = np.random.default_rng(41)
+    n = 25000
+    long_a = (rng.choice(n, size=20000, replace=False) + 1) * rng.choice([-1, 1], size=20000)
+    long_b = (rng.choice(n, size=5000, replace=False) + 1) * rng.choice([-1, 1], size=5000)
+    base = uniform_ksat(n, 3000, 3, seed=42)
+    cl = base.clauses() + [[int(v) for v in long_a], [int(v) for v in long_b]]
+    cnf = Cnf.from_clauses(n, cl, weights=rng.integers(1, 9, size=len(cl)))
+    got, _ = check_bit_exact(oracle, cnf, 4, 6, 5e-2)
+    with pkg.Solver.from_cnf(cnf, restarts=4, lr=5e-2) as s:
+        s.step(6, want_loss=False)
+        _, cost = s.step(0, want_loss=False)
+        assert np.array_equal(s.evaluate_x("dense").cpu().numpy(), cost)
+        s.check()
+    assert np.array_equal(cost, got["cost_hist"][-1])
+
+
 def test_planted_instance_reaches_zero_and_freezes(pkg, oracle):
     cnf = planted_ksat(40, 120, 3, seed=1)
     got, ref = check_bit_exact(oracle, cnf, 4, 400, 5e-2)
