@@ -88,6 +88,13 @@ typedef struct {
                            bytes <= 48 KiB; 0 = 256)                            */
     int32_t loss_norm;  /* MSAT_LOSS_MEAN_UNSAT (default), MSAT_LOSS_SUM_UNSAT
                            or MSAT_LOSS_MEAN_ALL; see below                    */
+    int32_t row_order;  /* rows of the stored w_j f_j: 0 = automatic (grouped
+                           by the variable pass's blocks when the store
+                           exceeds 32 MiB, else clause order), 1 = clause
+                           order, 2 = grouped by block.  x, costs and best
+                           are the same bits either way (the loss is summed
+                           in row order, within 1e-5); grouping puts about
+                           a third of a block's gathers in one window      */
 } msat_config;
 
 /* Normaliser N of the loss L = sum_{j in U} w_j f_j^2 / N and of its

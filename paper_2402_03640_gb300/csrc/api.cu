@@ -200,6 +200,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (cfg.heavy_deg < 0) return fail(MSAT_EINVAL, "msat_create: heavy_deg < 0");
     if (cfg.loss_norm < MSAT_LOSS_MEAN_UNSAT || cfg.loss_norm > MSAT_LOSS_MEAN_ALL)
         return fail(MSAT_EINVAL, "msat_create: unknown loss_norm");
+    if (cfg.row_order < 0 || cfg.row_order > 2) return fail(MSAT_EINVAL, "msat_create: unknown row_order");
     const int32_t leaf_room = 32 * (task_cap / GS);  // occurrences of the longest light variable
     const int32_t heavy_deg = std::min(cfg.heavy_deg > 0 ? cfg.heavy_deg : kLightMaxDeg,
                                        std::min(leaf_room, kLightMaxDeg));
@@ -242,6 +243,20 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     // expanded occurrence record streamed with the occurrence list
     const bool expand = cfg.f_mode == MSAT_F_EXPANDED ||
                         (cfg.f_mode == MSAT_F_AUTO && !use_fstore && kfix == 3 && m < (1LL << 28));
+    // rows of the store grouped by the variable pass's light blocks (the
+    // occurrence words carry rows; every sum keeps its order): by default
+    // when the store is above 32 MiB and so mostly gathered from HBM;
+    // never for the serving engine's contexts (their batched kernels read
+    // clause order)
+    const bool block_rows = use_fstore && !expand && !pool_alloc &&
+                            (cfg.row_order == 2 ||
+                             (cfg.row_order == 0 && (double)m * B * sizeof(float) > 32.0 * (1 << 20)));
+    RowOrder ro;
+    if (block_rows) {
+        const int rrc = build_block_rows(n_vars, m, kfix, coff, lit, weights, lblk, ro);
+        if (rrc) return rrc;
+        occ_to_rows(occ, ro);
+    }
     std::vector<int2> occx;
     if (expand) {
         occx.resize((size_t)nnz);
@@ -280,6 +295,8 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     int32_t *d_coff = nullptr, *d_lit = nullptr, *d_voff = nullptr, *d_occ = nullptr;
     int32_t *d_hvar = nullptr, *d_hch = nullptr;
     int2 *d_lblk = nullptr, *d_occx = nullptr;
+    int32_t *d_plit = nullptr, *d_pcoff = nullptr;
+    int64_t *d_pw = nullptr;
     int64_t *d_w = nullptr;
 #define TRY_ALLOC(ptr, count)                          \
     do {                                               \
@@ -295,6 +312,11 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     TRY_ALLOC(d_hch, (int64_t)hchunk0.size());
     TRY_ALLOC(d_lblk, (int64_t)lblk.size());
     if (expand) TRY_ALLOC(d_occx, nnz);
+    if (block_rows) {
+        TRY_ALLOC(d_plit, nnz);
+        if (kfix == 0) TRY_ALLOC(d_pcoff, m + 1);
+        if (weights) TRY_ALLOC(d_pw, m);
+    }
     if (use_fstore) TRY_ALLOC(c->S.fstore, m * B);
     TRY_ALLOC(c->S.x, nB);
     TRY_ALLOC(c->S.mom, nB);
@@ -326,6 +348,9 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     I.fwd_vw = fwd_vw;
     I.stage_vw = stage_vw;
     I.lblk = d_lblk;
+    I.plit = d_plit;
+    I.pcoff = d_pcoff;
+    I.pw = d_pw;
 
     DevStep &D = c->D;
     D.fwd_blocks = cfg.fwd_blocks > 0 ? cfg.fwd_blocks : fwd_grid_blocks(I);
@@ -375,6 +400,9 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (!e) e = up(d_hch, hchunk0.data(), sizeof(int32_t) * hchunk0.size());
     if (!e) e = up(d_lblk, lblk.data(), sizeof(int2) * lblk.size());
     if (!e && expand) e = up(d_occx, occx.data(), sizeof(int2) * occx.size());
+    if (!e && block_rows) e = up(d_plit, ro.plit.data(), sizeof(int32_t) * ro.plit.size());
+    if (!e && d_pcoff) e = up(d_pcoff, ro.pcoff.data(), sizeof(int32_t) * ro.pcoff.size());
+    if (!e && d_pw) e = up(d_pw, ro.pw.data(), sizeof(int64_t) * ro.pw.size());
     if (!e) e = up(D.sc, &sc, sizeof(sc));
     if (!e) e = up(D.best, best.data(), sizeof(long long) * best.size());
     if (!e) e = cudaMemsetAsync(D.best_step, 0, sizeof(long long) * (size_t)B, st);

@@ -232,3 +232,90 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
 }
 
 }  // namespace msat
+
+namespace msat {
+
+int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, const I32Buf &lit,
+                     const int64_t *w, const std::vector<int2> &lblk, RowOrder &ro) {
+    // light block of every light variable (-1: heavy)
+    std::vector<int32_t> vblk((size_t)n, -1);
+    for (size_t b = 0; b < lblk.size(); ++b)
+        for (int32_t v = lblk[b].x; v < lblk[b].y; ++v) vblk[(size_t)v] = (int32_t)b;
+    const int32_t nb = (int32_t)lblk.size();
+    // home block of each clause: that of its first light variable (nb: none)
+    ro.row.alloc((size_t)m);
+    std::vector<int32_t> home((size_t)m);
+    const int T = threads_for(m);
+    std::vector<std::vector<int64_t>> cnt((size_t)T, std::vector<int64_t>((size_t)nb + 1, 0));
+    parallel_ranges(m, T, [&](int t, int64_t b, int64_t e) {
+        for (int64_t j = b; j < e; ++j) {
+            int32_t h = nb;
+            for (int32_t p = coff[(size_t)j]; p < coff[(size_t)j + 1]; ++p) {
+                const int32_t vb = vblk[(size_t)(lit[(size_t)p] >> 1)];
+                if (vb >= 0) {
+                    h = vb;
+                    break;
+                }
+            }
+            home[(size_t)j] = h;
+            ++cnt[(size_t)t][(size_t)h];
+        }
+    });
+    // rows grouped by home block, clause order inside a group (stable):
+    // thread t's clauses of home h start after every earlier thread's.
+    // The groups run from the last light block down to the first, then the
+    // clauses with no light variable: the clause pass writes the rows of
+    // the variable pass's first blocks last, so more of them are still in
+    // L2 when that pass starts.
+    int64_t at = 0;
+    for (int32_t g = 0; g <= nb; ++g)
+        for (int t = 0; t < T; ++t) {
+            const int32_t h = g < nb ? nb - 1 - g : nb;
+            const int64_t k = cnt[(size_t)t][(size_t)h];
+            cnt[(size_t)t][(size_t)h] = at;
+            at += k;
+        }
+    parallel_ranges(m, T, [&](int t, int64_t b, int64_t e) {
+        std::vector<int64_t> &c = cnt[(size_t)t];
+        for (int64_t j = b; j < e; ++j) ro.row[(size_t)j] = (int32_t)c[(size_t)home[(size_t)j]]++;
+    });
+    // the clause pass's arrays in row order
+    const int64_t nnz = (int64_t)lit.size();
+    ro.plit.alloc((size_t)nnz);
+    if (kfix > 0) {
+        parallel_ranges(m, T, [&](int, int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; ++j)
+                for (int32_t p = 0; p < kfix; ++p)
+                    ro.plit[(size_t)ro.row[(size_t)j] * kfix + p] = lit[(size_t)j * kfix + p];
+        });
+    } else {
+        std::vector<int32_t> len((size_t)m);
+        for (int64_t j = 0; j < m; ++j) len[(size_t)ro.row[(size_t)j]] = coff[(size_t)j + 1] - coff[(size_t)j];
+        ro.pcoff.alloc((size_t)m + 1);
+        ro.pcoff[0] = 0;
+        for (int64_t r = 0; r < m; ++r) ro.pcoff[(size_t)r + 1] = ro.pcoff[(size_t)r] + len[(size_t)r];
+        parallel_ranges(m, T, [&](int, int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; ++j) {
+                int32_t q = ro.pcoff[(size_t)ro.row[(size_t)j]];
+                for (int32_t p = coff[(size_t)j]; p < coff[(size_t)j + 1]; ++p) ro.plit[(size_t)q++] = lit[(size_t)p];
+            }
+        });
+    }
+    if (w) {
+        ro.pw.assign((size_t)m, 0);
+        for (int64_t j = 0; j < m; ++j) ro.pw[(size_t)ro.row[(size_t)j]] = w[j];
+    }
+    return MSAT_OK;
+}
+
+void occ_to_rows(I32Buf &occ, const RowOrder &ro) {
+    const int64_t nnz = (int64_t)occ.size();
+    parallel_ranges(nnz, threads_for(nnz), [&](int, int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t o = occ[(size_t)q];
+            occ[(size_t)q] = (ro.row[(size_t)(o >> 1)] << 1) | (o & 1);
+        }
+    });
+}
+
+}  // namespace msat

@@ -1,6 +1,7 @@
 // Host-side CNF preparation of msat_create (host_cnf.cu).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <memory>
@@ -48,5 +49,24 @@ struct HostCnf {
 // input order.  The work is spread over the host's hardware threads.
 int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
                    HostCnf &out);
+
+// Rows of the clause pass's store of w*f grouped by the variable pass's
+// light blocks: a clause's home is the block of its first light variable
+// (clauses with none come last), the groups run from the last block down to
+// the first and keep clause order inside.  row[j] is clause j's row; plit (and pcoff
+// for clauses of different lengths, pw for weights) are the clause arrays
+// in row order, which the clause pass reads.
+struct RowOrder {
+    I32Buf row;               // [m]
+    I32Buf plit;              // [nnz]
+    I32Buf pcoff;             // [m+1], empty when every clause has kfix literals
+    std::vector<int64_t> pw;  // [m] or empty
+};
+
+int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, const I32Buf &lit,
+                     const int64_t *w, const std::vector<int2> &lblk, RowOrder &ro);
+
+// Occurrence words clause << 1 | neg become row << 1 | neg.
+void occ_to_rows(I32Buf &occ, const RowOrder &ro);
 
 }  // namespace msat

@@ -817,8 +817,16 @@ static cudaError_t launch_forward_vw(const DevInst &I, const DevState &S, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const DevInst &I, const DevState &S, const DevStep &D, int mode,
+cudaError_t launch_forward(const DevInst &I0, const DevState &S, const DevStep &D, int mode,
                            const float *t_override, cudaStream_t st) {
+    // with the store's rows grouped by block, the clause pass walks the
+    // clauses in row order (its item index is the row it writes)
+    DevInst I = I0;
+    if (I0.plit) {
+        I.lit = I0.plit;
+        I.coff = I0.pcoff ? I0.pcoff : I0.coff;
+        I.w = I0.pw;
+    }
     switch (I.fwd_vw) {
         case 8: return launch_forward_vw<8>(I, S, D, mode, t_override, st);
         case 4: return launch_forward_vw<4>(I, S, D, mode, t_override, st);
@@ -1549,7 +1557,7 @@ size_t small_smem_bytes(const DevInst &I) {
 }
 
 bool small_fits(const DevInst &I, int max_deg) {
-    return I.B <= kSmallMaxB && small_smem_bytes(I) <= kSmallSmemMax && max_deg <= 32 * 1023 &&
+    return !I.plit && I.B <= kSmallMaxB && small_smem_bytes(I) <= kSmallSmemMax && max_deg <= 32 * 1023 &&
            (long long)I.m * I.B <= (1LL << 30);
 }
 

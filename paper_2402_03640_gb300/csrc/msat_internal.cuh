@@ -53,6 +53,12 @@ struct DevInst {
     int32_t fwd_vw;               // restarts per thread in the clause pass
     int32_t stage_vw;             // restarts per thread of a light-variable leaf task
     const int2 *lblk;             // [n_lblk] variable range [x, y) of each light block
+    // stored w*f with rows grouped by light block (or nullptr: row = clause):
+    // the clause arrays in row order, which the clause pass reads instead
+    // of lit / coff / w; the occurrence words then carry rows, not clauses
+    const int32_t *plit;          // [nnz]
+    const int32_t *pcoff;         // [m+1] or nullptr (every clause has kfix literals)
+    const int64_t *pw;            // [m] or nullptr (all weights 1)
 };
 
 // Scalars of the optimizer step shared by all restarts.
@@ -88,7 +94,7 @@ struct DevStep {
 struct DevState {
     float *x, *mom, *vel;  // [n][B]
     float *t0, *t1;        // double-buffered tanh(x), [n][B]
-    uint32_t *ubits;       // unsat bits, flat index j*B + b
+    uint32_t *ubits;       // unsat bits, flat index row*B + b (row = j unless grouped)
     uint8_t *bestx;        // [n][B] best assignment (0/1)
     float *fstore;         // [m][B] of the last clause pass: (float)w_j * f_j where clause
                            // j is unsat for restart b, NaN where it is satisfied; or

@@ -41,7 +41,8 @@ class msat_config(ctypes.Structure):
                 ("f_mode", ctypes.c_int32), ("seed_x", ctypes.c_uint64),
                 ("heavy_deg", ctypes.c_int32), ("fwd_vw", ctypes.c_int32),
                 ("stage_vw", ctypes.c_int32), ("fwd_blocks", ctypes.c_int32),
-                ("light_rows", ctypes.c_int32), ("loss_norm", ctypes.c_int32)]
+                ("light_rows", ctypes.c_int32), ("loss_norm", ctypes.c_int32),
+                ("row_order", ctypes.c_int32)]
 
 
 class msat_tune_entry(ctypes.Structure):

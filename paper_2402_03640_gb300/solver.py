@@ -25,7 +25,8 @@ def _p(a) -> Optional[ctypes.c_void_p]:
 
 
 def _config(restarts=1, seed_x=1, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, f_mode="auto",
-            heavy_deg=0, fwd_vw=0, stage_vw=0, fwd_blocks=0, light_rows=0, loss_norm="mean_unsat"):
+            heavy_deg=0, fwd_vw=0, stage_vw=0, fwd_blocks=0, light_rows=0, loss_norm="mean_unsat",
+            row_order="auto"):
     lib = native.load()
     cfg = native.msat_config()
     check(lib.msat_config_default(ctypes.byref(cfg)))
@@ -37,6 +38,7 @@ def _config(restarts=1, seed_x=1, lr=1e-4, beta1=0.9, beta2=0.999, eps=1e-8, f_m
     cfg.fwd_vw, cfg.stage_vw = int(fwd_vw), int(stage_vw)
     cfg.fwd_blocks, cfg.light_rows = int(fwd_blocks), int(light_rows)
     cfg.loss_norm = native.LOSS_NORMS[loss_norm]
+    cfg.row_order = {"auto": 0, "clause": 1, "block": 2}[row_order]
     return cfg
 
 
@@ -66,12 +68,13 @@ class Solver:
                  lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
                  stream=None, f_mode: str = "auto", heavy_deg: int = 0, fwd_vw: int = 0,
                  stage_vw: int = 0, fwd_blocks: int = 0, light_rows: int = 0,
-                 loss_norm: str = "mean_unsat", tune: bool = False):
+                 loss_norm: str = "mean_unsat", tune: bool = False, row_order: str = "auto"):
         lib = native.load()
         self._lib = lib
         cfg = _config(restarts=restarts, seed_x=seed_x, lr=lr, beta1=beta1, beta2=beta2, eps=eps,
                       f_mode=f_mode, heavy_deg=heavy_deg, fwd_vw=fwd_vw, stage_vw=stage_vw,
-                      fwd_blocks=fwd_blocks, light_rows=light_rows, loss_norm=loss_norm)
+                      fwd_blocks=fwd_blocks, light_rows=light_rows, loss_norm=loss_norm,
+                      row_order=row_order)
         off = np.ascontiguousarray(off, dtype=np.int64)
         lits = np.ascontiguousarray(lits, dtype=np.int32)
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.int64)

@@ -111,6 +111,20 @@ def test_f_modes_identical(pkg, oracle, f_mode, B):
     check_bit_exact(oracle, cnf, B, 12, 2e-2, f_mode=f_mode)
 
 
+@pytest.mark.parametrize("B", [1, 8, 16, 64])
+def test_store_rows_grouped_by_block(pkg, oracle, B):
+    """The store's rows grouped by the variable pass's light blocks (the
+    occurrence words carry rows, the clause pass reads row-ordered clause
+    arrays): the same bits as clause order, on fixed-length clauses with
+    several light blocks and on weighted mixed-length clauses with heavy
+    variables (clauses whose variables are all heavy come last)."""
+    cnf = uniform_ksat(3000, 12900, 3, seed=51)
+    got, _ = check_bit_exact(oracle, cnf, B, 12, 5e-2, row_order="block", light_rows=64)
+    assert got["info"]["small_kernel"] == 0
+    z = zipf_weighted(2500, 9000, seed=52)
+    check_bit_exact(oracle, z, B, 8, 2e-2, row_order="block", heavy_deg=16)
+
+
 @pytest.mark.parametrize("heavy_deg", [1, 8, 40])
 @pytest.mark.parametrize("f_mode", ["store", "recompute"])
 def test_heavy_split_identical(pkg, oracle, heavy_deg, f_mode):
