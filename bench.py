@@ -610,7 +610,7 @@ def measure_e2e(pkg, cnf, B, args, dense, ws, shape_kw):
 
 def dense_steady_state(pkg, sms=152, waves=8):
     """The tensor-core evaluator's own rate with whole waves of tiles: 3-SAT
-    with n = 5120 (40 k-steps a tile) and 128 * sms * waves clauses, 256
+    with n = 5120 (20 k-steps of 256 variables a tile) and 128 * sms * waves clauses, 256
     assignments (one assignment tile), so every CTA of the one-per-SM grid
     takes `waves` whole tiles and no tile is split; the packed clause matrix
     (50 MB per wave of tiles, 400 MB in all) is streamed from HBM.  Ten timed

@@ -634,7 +634,7 @@ static int dense_setup(msat_ctx *c) {
             return fail(MSAT_EINVAL, "msat_evaluate: the dense backend needs clause weights below 2^25");
     DenseDev &d = c->dense;
     d.m_pad = (int)std::max<int64_t>(128, (c->m + 127) / 128 * 128);
-    d.n_pad = (c->n + 127) / 128 * 128;
+    d.n_pad = (c->n + kDenseKStep - 1) / kDenseKStep * kDenseKStep;
     const double bytes = (double)d.m_pad * (double)d.n_pad / 2;
     if (bytes > 64.0 * (1LL << 30))
         return fail(MSAT_EINVAL, "msat_evaluate: the dense clause matrix would take " +

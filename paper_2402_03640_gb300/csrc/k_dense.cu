@@ -8,21 +8,24 @@
 //
 // tcgen05.mma .kind::i8 is not available on sm_103a, so both operands are
 // e2m1 (0, +1, -1 are exact) with fp32 accumulation, which is exact here:
-// every partial sum is an integer of magnitude <= n < 2^24.  In global
-// memory the operands are packed, two 4-bit codes a byte; the TMA loads
-// (tensor maps of type 16U4_ALIGN16B) expand them into the padded layout
-// .kind::f8f6f4 reads (16 codes in the first 8 bytes of each 16-byte
-// chunk), so shared memory holds one byte per element as with 8-bit types
-// while HBM, L2 and the path into each SM carry half the bytes.
+// every partial sum is an integer of magnitude <= n < 2^24.  The MMA kind
+// is the block-scaled .kind::mxf4 with every scale factor 1 (ue8m0 code
+// 127 = 2^0), so D = A B exactly.  It reads the operands packed, two 4-bit
+// codes a byte, the form they have in global memory: HBM, L2, the TMA
+// copies and shared memory all carry half a byte per element.  A and B
+// pack variable i the same way (low nibble for even i), so the pairing of
+// nibbles with k inside the MMA cannot change a dot product.
 //
-// Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 128
-// variables per stage.  Warp 0 (one lane) loads A and B tiles with TMA into
-// a 4-stage ring of 128B-swizzled shared-memory buffers; warp 1 (one lane)
-// issues tcgen05.mma into one of two TMEM accumulators and releases each
-// stage with tcgen05.commit; warps 2-5 read the accumulator with tcgen05.ld
-// (one TMEM lane quarter each), compare with -len_j and reduce the weighted
-// unsat counts per column, while the next segment accumulates into the
-// other buffer.
+// Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 256
+// variables per stage (128 bytes a row).  Warp 0 (one lane) loads A and B
+// tiles with TMA into a 4-stage ring of 128B-swizzled shared-memory
+// buffers; warp 1 (one lane) issues tcgen05.mma into a TMEM accumulator
+// and releases each stage with tcgen05.commit; warps 2-5 write the scale
+// factors into TMEM once, then read the accumulator with tcgen05.ld (one
+// TMEM lane quarter each), compare with -len_j and reduce the weighted
+// unsat counts per column.  With N <= 240 there are two accumulators and
+// the next segment accumulates into the other one meanwhile; at N = 256
+// the 512 TMEM columns hold one accumulator and the scale factors.
 //
 // Schedule: with more tiles than SMs, every CTA of a one-per-SM grid takes
 // the same number of whole tiles, and when the leftover tiles would fill at
@@ -56,9 +59,12 @@ namespace msat {
 namespace {
 
 constexpr int kTM = 128;            // clauses per tile (MMA M)
-constexpr int kTK = 128;            // variables per stage (128 bytes a row in shared memory)
+constexpr int kTK = kDenseKStep;    // variables per stage (256: 128 bytes a row in shared memory)
+constexpr int kRowBytes = kTK / 2;  // packed bytes of a row per stage
+constexpr int kSfCols = 32;         // TMEM columns of scale factors (A: first 16, B: last 16)
+constexpr uint32_t kSfOne = 0x7F7F7F7Fu;  // four ue8m0 scale factors of 2^0
 constexpr int kStages = 4;
-constexpr int kAccBufs = 2;         // TMEM accumulators (segment j uses j % 2)
+constexpr int kAccBufs = 2;         // TMEM accumulators at most (segment j uses j % bufs)
 constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
@@ -174,22 +180,25 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor of kind::f8f6f4: D fp32, A and B e2m1, both
-// K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_e2m1(int n) {
-    return (1u << 4)                      // D format fp32
-           | (5u << 7) | (5u << 10)       // A, B format e2m1
+// Instruction descriptor of the block-scaled kind::mxf4: A and B e2m1
+// (format 1), both K-major, scale factors ue8m0 (bit 23), scale-factor
+// byte 0 of A and of B, M = 128, N = n, dense K = 64 per MMA.
+__device__ __forceinline__ uint32_t idesc_mxf4(int n) {
+    return (1u << 7) | (1u << 10)         // A, B format e2m1
            | ((uint32_t)(n >> 3) << 17)   // N / 8
+           | (1u << 23)                   // scale factors ue8m0
            | ((uint32_t)(kTM >> 4) << 24);  // M / 16
 }
 
-__device__ __forceinline__ void mma_f8f6f4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (+)= (A x SFA) (B x SFB), K = 64 codes (32 bytes of each row).
+__device__ __forceinline__ void mma_mxf4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t tmem_sfa, uint32_t tmem_sfb, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(tmem_sfa), "r"(tmem_sfb)
         : "memory");
 }
 
@@ -211,6 +220,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Writes v into 32 consecutive columns of the warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // One segment of a CTA's work: k-steps [ka, kb) of tile `tile`; tr is the
@@ -252,8 +272,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     DenseHeader *H = reinterpret_cast<DenseHeader *>(base);
     uint8_t *stages = base + kHeader;
     const int ntile = d.ntile;
-    const uint32_t a_bytes = kTM * kTK;
-    const uint32_t b_bytes = (uint32_t)ntile * kTK;
+    const uint32_t a_bytes = kTM * kRowBytes;
+    const uint32_t b_bytes = (uint32_t)ntile * kRowBytes;
+    // accumulators of tmem_cols columns each, then the scale factors
+    const int nbuf = 2 * tmem_cols + kSfCols <= 512 ? kAccBufs : 1;
+    const int sf_col = nbuf * tmem_cols;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cta = blockIdx.x;
@@ -263,7 +286,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             mbar_init(&H->full[s], 1);
             mbar_init(&H->empty[s], 1);
         }
-        for (int b = 0; b < kAccBufs; ++b) {
+        for (int b = 0; b < nbuf; ++b) {
             mbar_init(&H->acc_full[b], 1);
             mbar_init(&H->acc_empty[b], 4);  // one arrive per epilogue warp
         }
@@ -274,9 +297,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int c = threadIdx.x; c < 256; c += blockDim.x) H->colsum[c] = 0ull;
-    if (warp == 1) {
+    if (warp == 1) {  // all 512 columns (one CTA per SM)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&H->tmem)),
-                     "r"(kAccBufs * tmem_cols)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -285,21 +308,27 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     tc_fence_after();
     const uint32_t tmem = H->tmem;
     const int nseg = seg_count(d, cta);
+    // scale factors 2^0 in every byte of the scale-factor columns, written
+    // before the first MMA is issued
+    if (warp >= 2) tmem_fill32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)sf_col, kSfOne);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0 && lane == 0) {
         // producer: TMA loads of the A (clause rows) and B (assignment rows)
         // tiles of every segment in turn; the A tiles are prefetched into L2
-        // kPrefetch k-tiles ahead within a segment (x = kt * 128 codes: 64
-        // bytes, 16-byte aligned)
+        // kPrefetch k-tiles ahead within a segment (x = kt * 128 bytes,
+        // 16-byte aligned)
         int it = 0;
         bool stop = false;
         for (int j = 0; j < nseg && !stop; ++j) {
             const DenseSeg g = seg_at(d, cta, j);
             const int m0 = (g.tile % d.tiles_m) * kTM, n0 = (g.tile / d.tiles_m) * ntile;
-            for (int kt = g.ka; kt < g.kb && kt < g.ka + kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kTK, m0);
+            for (int kt = g.ka; kt < g.kb && kt < g.ka + kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kRowBytes, m0);
             for (int kt = g.ka; kt < g.kb; ++kt) {
                 const int s = it % kStages;
-                if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kTK, m0);
+                if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kRowBytes, m0);
                 if (it >= kStages) {
                     const uint32_t parity = (uint32_t)((it / kStages - 1) & 1);
                     if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, 0, kWaitNs)) {
@@ -310,11 +339,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
                     }
                 }
                 uint8_t *sa = stages + (size_t)s * stage_bytes;
-                // the transaction count of a packed-type load is the bytes it
-                // reads (two codes a byte), half what it writes to shared memory
-                mbar_expect_tx(&H->full[s], stage_bytes / 2);
-                tma_load_2d(sa, &tmA, kt * kTK, m0, &H->full[s]);
-                tma_load_2d(sa + a_bytes, &tmB, kt * kTK, n0, &H->full[s]);
+                mbar_expect_tx(&H->full[s], stage_bytes);
+                tma_load_2d(sa, &tmA, kt * kRowBytes, m0, &H->full[s]);
+                tma_load_2d(sa + a_bytes, &tmB, kt * kRowBytes, n0, &H->full[s]);
                 ++it;
             }
         }
@@ -322,16 +349,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         for (int i = (it > kStages ? it - kStages : 0); i < it; ++i)
             if (!mbar_wait(&H->full[i % kStages], (uint32_t)((i / kStages) & 1), 0, kWaitNs)) atomicOr(errflag, 2u);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: segment j accumulates into TMEM buffer j % 2 once the
-        // epilogue has read what the segment before last left there
-        const uint32_t idesc = idesc_e2m1(ntile);
+        // MMA issuer: segment j accumulates into TMEM buffer j % nbuf once
+        // the epilogue has read what segment j - nbuf left there
+        const uint32_t idesc = idesc_mxf4(ntile);
+        const uint32_t sfa = tmem + (uint32_t)sf_col, sfb = sfa + (uint32_t)(kSfCols / 2);
         int it = 0;
         bool stop = false;
         for (int j = 0; j < nseg && !stop; ++j) {
             const DenseSeg g = seg_at(d, cta, j);
-            const int buf = j % kAccBufs;
-            if (j >= kAccBufs &&
-                !mbar_wait_abort(&H->acc_empty[buf], (uint32_t)((j / kAccBufs - 1) & 1), &H->abort)) {
+            const int buf = j % nbuf;
+            if (j >= nbuf && !mbar_wait_abort(&H->acc_empty[buf], (uint32_t)((j / nbuf - 1) & 1), &H->abort)) {
                 H->abort = 1;
                 atomicOr(errflag, 1u);
                 stop = true;
@@ -352,8 +379,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
                 const uint64_t adesc = smem_desc_sw128(sa);
                 const uint64_t bdesc = smem_desc_sw128(sa + a_bytes);
 #pragma unroll
-                for (int kk = 0; kk < kTK / 32; ++kk)  // K = 32 codes per MMA: +2 in the 16-byte address field
-                    mma_f8f6f4(acc, adesc + 2 * kk, bdesc + 2 * kk, idesc, (kt != g.ka || kk != 0) ? 1u : 0u);
+                for (int kk = 0; kk < kRowBytes / 32; ++kk)  // K = 64 codes (32 bytes) per MMA: +2 in the 16-byte address field
+                    mma_mxf4(acc, adesc + 2 * kk, bdesc + 2 * kk, idesc, sfa, sfb, (kt != g.ka || kk != 0) ? 1u : 0u);
                 mma_commit(&H->empty[s]);
                 ++it;
             }
@@ -375,8 +402,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         const int etid = threadIdx.x - 64;
         for (int j = 0; j < nseg; ++j) {
             const DenseSeg g = seg_at(d, cta, j);
-            const int buf = j % kAccBufs;
-            const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / kAccBufs) & 1), &H->abort);
+            const int buf = j % nbuf;
+            const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / nbuf) & 1), &H->abort);
             if (!ok) H->epi_fail = 1;
             epi_sync();
             if (H->epi_fail) {  // the same decision in all four warps
@@ -452,7 +479,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
                     if (etid == 0) part_cnt[g.tr] = 0u;  // ready for the next launch
                 }
             }
-            // the accumulator buffer is free for the segment after next
+            // the accumulator buffer is free for segment j + nbuf
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&H->acc_empty[buf]);
@@ -472,8 +499,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccBufs * tmem_cols)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier that
@@ -492,7 +518,7 @@ __global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
 
 // Per-piece targets of the split tiles: for split tile tr, piece p and row
 // r, minus the number of the clause's literals whose variable lies in the
-// piece's k-range [p * kt / split, (p + 1) * kt / split) x 128 (NaN for
+// piece's k-range [p * kt / split, (p + 1) * kt / split) x kTK (NaN for
 // padding rows and for clauses that never count).
 __global__ void k_dense_piece_targets(DevInst I, const float *__restrict__ target, DenseSched d, int grid,
                                       float *__restrict__ ptgt) {
@@ -603,16 +629,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2D tensor of packed 4-bit codes [rows][cols] (cols contiguous, cols / 2
-// bytes a row; cols a multiple of 128), box 128 x box_rows, expanded into
-// the padded shared-memory layout with 128B swizzle.
+// bytes a row; cols a multiple of kTK), copied as bytes: box kRowBytes x
+// box_rows, 128B swizzle, landing in shared memory as packed as it is in
+// global memory.
 int encode_2d(CUtensorMap *map, void *base, long long cols, long long rows, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return fail(MSAT_ECUDA, "dense backend: cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    if (cols % kTK != 0) return fail(MSAT_EINVAL, "dense backend: padded variable count is not a multiple of 256");
+    const cuuint64_t dims[2] = {(cuuint64_t)(cols / 2), (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(cols / 2)};
-    const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B, 2, base, dims, strides, box, estr,
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
@@ -633,7 +661,7 @@ int dense_rows(int nb) {
 }
 
 size_t dense_smem_bytes(int ntile) {
-    return 1024 + kHeader + (size_t)kStages * ((size_t)kTM * kTK + (size_t)ntile * kTK);
+    return 1024 + kHeader + (size_t)kStages * ((size_t)kTM + (size_t)ntile) * kRowBytes;
 }
 
 int dense_encode_a(DenseDev &d) { return encode_2d(&d.tmA, d.Wt, d.n_pad, d.m_pad, kTM); }
@@ -687,8 +715,7 @@ DenseSched dense_plan(const DenseDev &d, int ntile, int *grid) {
         int split = rest > 0 ? G / rest : 0;
         if (split > 4) split = 4;
         if (split > p.kt_count) split = p.kt_count;
-        // a piece's sums must fit int16: at most 255 k-steps of 128
-        if (rest > 0 && split >= 2 && (p.kt_count + split - 1) / split <= 255) {
+        if (rest > 0 && split >= 2) {
             p.full = full;
             p.tail = rest;
             p.split = split;
@@ -705,7 +732,7 @@ cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaSt
     const size_t smem = dense_smem_bytes(ntile);
     e = cudaFuncSetAttribute(k_dense_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_dense());
     if (e) return e;
-    int tmem_cols = 32;
+    int tmem_cols = 32;  // one accumulator's columns
     while (tmem_cols < ntile) tmem_cols <<= 1;
     int grid = 0;
     const DenseSched p = dense_plan(d, ntile, &grid);

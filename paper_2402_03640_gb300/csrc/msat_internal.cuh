@@ -110,8 +110,11 @@ struct DevState {
 // takes whole tiles j * grid + c for j < full, then (c < tail_ctas) piece
 // c % split of split tile c / split: k-steps [piece * kt_count / split,
 // (piece + 1) * kt_count / split) of tile full * grid + c / split.
+// Variables per k-step of the dense evaluation (n is padded to a multiple).
+constexpr int kDenseKStep = 256;
+
 struct DenseSched {
-    int kt_count;   // k-steps (128 variables) per tile
+    int kt_count;   // k-steps (kDenseKStep variables) per tile
     int tiles_m;
     int ntile;      // assignments per tile
     int full;

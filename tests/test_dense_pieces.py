@@ -73,16 +73,16 @@ def test_piece_targets_equal_the_unsat_test(seed):
 
 
 def test_piece_targets_at_k_step_boundaries():
-    """The split the kernel uses: 128-variable k-steps dealt into `split`
+    """The split the kernel uses: 256-variable k-steps dealt into `split`
     equal ranges of k-steps (piece p covers k-steps [p*kt/split,
-    (p+1)*kt/split)); n not a multiple of 128."""
+    (p+1)*kt/split)); n not a multiple of 256."""
     rng = np.random.default_rng(7)
-    n, kt = 1000, (1000 + 127) // 128
+    n, kt = 1000, (1000 + 255) // 256
     cnf = uniform_ksat(n, 600, 5, seed=3)
     clauses = [_canonical(c) for c in cnf.clauses()] + [list(range(1, n + 1, 9)), []]
     a01 = rng.integers(0, 2, size=(48, n)).astype(np.uint8)
     want = _unsat_by_definition(clauses, a01)
     for split in (2, 3, 4):
-        bounds = [min(n, (p * kt // split) * 128) for p in range(split + 1)]
+        bounds = [min(n, (p * kt // split) * 256) for p in range(split + 1)]
         bounds[-1] = n
         assert np.array_equal(_pieces_test(clauses, n, a01, bounds), want), split
