@@ -87,16 +87,48 @@ def algorithmic_bytes(cnf, B):
     return {"forward": fwd, "backward": bwd}
 
 
+# nominal dense tensor rates of the part: fp4 13.5 and bf16 2.25 PFLOP/s
+FP4_PER_BF16 = 13.5 / 2.25
+
+
 def measured_peaks():
-    """(HBM GB/s, source), (fp8 dense TFLOP/s, source): the copy bandwidth and
-    the bf16 GEMM rate measured on these GPUs, fp8 taken as twice bf16 (the
-    nominal ratio of the dense tensor rates)."""
+    """(HBM GB/s, source), (fp4 dense TFLOP/s, source): the copy bandwidth and
+    the bf16 GEMM rate measured on these GPUs, fp4 (the dense evaluator's
+    block-scaled e2m1 MMA) taken as bf16 times the nominal fp4:bf16 ratio."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return (float(d["hbm_gbs"]), "measured"), (2.0 * float(d["bf16_tflops"]), "measured bf16 x 2")
-    return (6800.0, "fallback"), (3800.0, "fallback bf16 x 2")
+        return ((float(d["hbm_gbs"]), "measured"),
+                (FP4_PER_BF16 * float(d["bf16_tflops"]), "measured bf16 x 6 (nominal fp4:bf16 ratio)"))
+    return (6800.0, "fallback"), (FP4_PER_BF16 * 1900.0, "fallback bf16 x 6 (nominal fp4:bf16 ratio)")
+
+
+def dense_roofline(pkg, m, n, B, avg_s, peak_gbs, tc_peak, tc_kind):
+    """Both bounds of one dense evaluation: the packed clause matrix W^T
+    (m x n e2m1 codes, half a byte each), the packed batch (B x n) and the
+    per-clause target and weight (8 bytes) read once, against HBM; 2 m n B
+    flops against the fp4 tensor peak.  The binding one is reported, with
+    the MMA rate of the evaluator's own instruction shape measured live
+    beside it."""
+    flops = 2.0 * m * n * B
+    nbytes = m * n / 2.0 + B * n / 2.0 + 8.0 * m
+    tf = flops / avg_s / 1e12
+    gbs = nbytes / avg_s / 1e9
+    t_tc, t_hbm = flops / (tc_peak * 1e12), nbytes / (peak_gbs * 1e9)
+    ntile = min(256, (B + 15) // 16 * 16)
+    inst = pkg.dense_mma_rate(ntile, 4096)
+    ent = {"avg_us": 1e6 * avg_s, "flops": flops, "tflops": tf, "bytes": nbytes, "gbs": gbs,
+           "tensor_frac": tf / tc_peak, "hbm_frac": gbs / peak_gbs, "peak_tflops": tc_peak,
+           "peak_source": tc_kind, "peak_gbs": peak_gbs,
+           "instruction_peak_tflops": inst, "instruction_frac": tf / inst,
+           "instruction_peak_source": f"msat_dense_mma_rate: kind::mxf4 M=128 N={ntile} K=64 issued back to "
+                                      "back on every SM, operands resident in shared memory"}
+    if t_tc >= t_hbm:
+        ent.update(bound="tensor", frac=tf / tc_peak)
+    else:
+        ent.update(bound="hbm", frac=gbs / peak_gbs)
+    return ent
 
 
 class ClockSampler:
@@ -484,12 +516,9 @@ def measure_workload(pkg, args, workload, ws, rank, with_cpu=True, with_e2e=True
         abytes["small_steps"] = by
     if dense and prof["evaluate"][0]:
         launches, ms = prof["evaluate"]
-        avg = ms / launches
-        flops = 2.0 * cnf.m * cnf.n * B  # multiply-adds of W^T X counted twice
-        tf = flops / (avg / 1e3) / 1e12
-        per_kernel["dense_eval"] = {"launches": launches, "avg_us": 1e3 * avg, "bound": "tensor",
-                                    "flops": flops, "tflops": tf, "frac": tf / tc_peak,
-                                    "peak_tflops": tc_peak, "peak_source": tc_kind}
+        per_kernel["dense_eval"] = dict(launches=launches, **dense_roofline(
+            pkg, cnf.m, cnf.n, B, ms / launches / 1e3, peak, tc_peak, tc_kind))
+        abytes["dense_eval"] = per_kernel["dense_eval"]["bytes"]
     dom = max(per_kernel, key=lambda k: per_kernel[k]["avg_us"] * per_kernel[k]["launches"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -504,6 +533,8 @@ def measure_workload(pkg, args, workload, ws, rank, with_cpu=True, with_e2e=True
         roofline = {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": ach / tc_peak, "traffic": traffic, "kernel": dom,
                     "peak_source": tc_kind, "algorithmic_flops_per_launch": per_kernel[dom]["flops"]}
+        if dom == "dense_eval":
+            roofline["instruction_peak"] = per_kernel[dom]["instruction_peak_tflops"]
     else:
         ach = per_kernel[dom]["gbs"]
         roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -614,7 +645,7 @@ def dense_steady_state(pkg, sms=152, waves=8):
     assignments (one assignment tile), so every CTA of the one-per-SM grid
     takes `waves` whole tiles and no tile is split; the packed clause matrix
     (50 MB per wave of tiles, 400 MB in all) is streamed from HBM.  Ten timed
-    launches after three untimed ones."""
+    launches after three untimed ones; both bounds as in dense_roofline."""
     import torch
     n, B = 5120, 256
     m = 128 * sms * waves
@@ -633,14 +664,11 @@ def dense_steady_state(pkg, sms=152, waves=8):
         s.profile(False)
         s.check()
     launches, ms = prof["evaluate"]
-    avg = ms / launches
-    flops = 2.0 * m * n * B
-    (_, _), (tc_peak, tc_kind) = measured_peaks()
-    tf = flops / (avg / 1e3) / 1e12
-    return {"workload": f"uniform 3-SAT n={n}, m={m} (seed 3), {B} assignments: {waves} waves of whole "
-                        f"128 x 256 tiles on {sms} SMs, no split tile",
-            "launches": launches, "avg_us": 1e3 * avg, "flops": flops, "tflops": tf, "frac": tf / tc_peak,
-            "peak_tflops": tc_peak, "peak_source": tc_kind}
+    (peak_gbs, _), (tc_peak, tc_kind) = measured_peaks()
+    ent = {"workload": f"uniform 3-SAT n={n}, m={m} (seed 3), {B} assignments: {waves} waves of whole "
+                       f"128 x 256 tiles on {sms} SMs, no split tile", "launches": launches}
+    ent.update(dense_roofline(pkg, m, n, B, ms / launches / 1e3, peak_gbs, tc_peak, tc_kind))
+    return ent
 
 
 def other_configs(pkg, args, rank):

@@ -272,6 +272,23 @@ int msat_check(msat_ctx *ctx);
 int msat_selftest_bounded_wait(int64_t spins);
 
 /*
+ * Measured peak of the dense backend's tensor-core instruction (no
+ * counterpart in the paper; a benchmark helper): every SM issues `iters`
+ * stages of four block-scaled kind::mxf4 MMAs (M = 128 clauses, N =
+ * n_assign assignments, K = 64 e2m1 codes, unit scale factors) on operands
+ * resident in shared memory, and the second of two launches is timed with
+ * CUDA events on the current device.  The dense evaluator runs the same
+ * instructions behind its TMA pipeline, so this rate bounds it.
+ *   n_assign   multiple of 16 in [16, 256]
+ *   iters      stages per SM, in [1, 2^20]
+ *   tflops     host double: 2 * 128 * n_assign * 64 * 4 * iters * SMs
+ *              divided by the launch time, in TFLOP/s
+ * Synchronous; allocates and frees one 4-byte flag.  EINVAL on bad
+ * arguments, ETIMEOUT if the bounded wait for the MMAs gave up.
+ */
+int msat_dense_mma_rate(int32_t n_assign, int32_t iters, double *tflops);
+
+/*
  * The paper's quick evaluation reads clause j as satisfied when f_j > 0
  * (Sec. 4, "Example": a positive clause value marks a satisfied clause);
  * the exact test is "some literal is true under x > 0" (Sec. 4,

@@ -6,6 +6,6 @@ hand-written CUDA kernels for sm_103a behind the C ABI in include/msat.h.
 This package is the thin binding: build (nvcc), native (ctypes), solver.
 """
 from .native import MsatError, library_path, load
-from .solver import Server, Solver, msat_loss
+from .solver import Server, Solver, dense_mma_rate, msat_loss
 
-__all__ = ["MsatError", "Server", "Solver", "library_path", "load", "msat_loss"]
+__all__ = ["MsatError", "Server", "Solver", "dense_mma_rate", "library_path", "load", "msat_loss"]

@@ -646,9 +646,11 @@ static int dense_setup(msat_ctx *c) {
     if ((rc = dalloc_t(c, &d.errflag, 1))) return rc;
     std::vector<float> tgt((size_t)d.m_pad, std::nanf(""));
     std::vector<uint32_t> w32((size_t)d.m_pad, 0u);
+    d.unit_w = true;
     for (int64_t j = 0; j < c->m; ++j) {
         if (!c->taut[(size_t)j]) tgt[(size_t)j] = -(float)c->clen[(size_t)j];
         w32[(size_t)j] = c->wts.empty() ? 1u : (uint32_t)c->wts[(size_t)j];
+        d.unit_w = d.unit_w && w32[(size_t)j] == 1u;
     }
     cudaStream_t st = c->stream;
     MSAT_CUDA_TRY(cudaMemsetAsync(d.Wt, 0, (size_t)d.m_pad * d.n_pad / 2, st));
@@ -995,6 +997,41 @@ extern "C" int msat_selftest_bounded_wait(int64_t spins) {
         return fail(MSAT_ETIMEOUT, "msat_selftest_bounded_wait: the wait gave up after " +
                                        (spins ? std::to_string(spins) + " tries" : std::string("its time limit")) +
                                        " (flag " + std::to_string(h) + ")");
+    return MSAT_OK;
+}
+
+extern "C" int msat_dense_mma_rate(int32_t n_assign, int32_t iters, double *tflops) {
+    if (!tflops) return fail(MSAT_EINVAL, "msat_dense_mma_rate: NULL argument");
+    if (n_assign < 16 || n_assign > 256 || n_assign % 16 != 0)
+        return fail(MSAT_EINVAL, "msat_dense_mma_rate: n_assign must be a multiple of 16 in [16, 256]");
+    if (iters < 1 || iters > (1 << 20)) return fail(MSAT_EINVAL, "msat_dense_mma_rate: iters must be in [1, 2^20]");
+    int dev = 0, sms = 0;
+    MSAT_CUDA_TRY(cudaGetDevice(&dev));
+    MSAT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned int *flag = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(unsigned));
+    if (e) return cuda_fail(e, "msat_dense_mma_rate: allocation");
+    float ms = 0.0f;
+    unsigned h = 0;
+    e = cudaMemset(flag, 0, sizeof(unsigned));
+    if (!e) e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    if (!e) e = launch_mma_rate(n_assign, iters, sms, flag, nullptr);  // warm-up
+    if (!e) e = cudaEventRecord(e0, nullptr);
+    if (!e) e = launch_mma_rate(n_assign, iters, sms, flag, nullptr);
+    if (!e) e = cudaEventRecord(e1, nullptr);
+    if (!e) e = cudaEventSynchronize(e1);
+    if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (!e) e = cudaMemcpy(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(flag);
+    if (e) return cuda_fail(e, "msat_dense_mma_rate");
+    if (h) return fail(MSAT_ETIMEOUT, "msat_dense_mma_rate: a wait gave up (flag " + std::to_string(h) + ")");
+    // four MMAs of 128 x n_assign x 64 multiply-adds a stage, on every SM
+    const double flops = 2.0 * 128.0 * n_assign * 64.0 * 4.0 * (double)iters * (double)sms;
+    *tflops = flops / ((double)ms * 1e-3) / 1e12;
     return MSAT_OK;
 }
 

@@ -19,13 +19,16 @@
 // Tile: 128 clauses x N assignments (N <= 256, a multiple of 16), K = 256
 // variables per stage (128 bytes a row).  Warp 0 (one lane) loads A and B
 // tiles with TMA into a 4-stage ring of 128B-swizzled shared-memory
-// buffers; warp 1 (one lane) issues tcgen05.mma into a TMEM accumulator
-// and releases each stage with tcgen05.commit; warps 2-5 write the scale
-// factors into TMEM once, then read the accumulator with tcgen05.ld (one
-// TMEM lane quarter each), compare with -len_j and reduce the weighted
-// unsat counts per column.  With N <= 240 there are two accumulators and
-// the next segment accumulates into the other one meanwhile; at N = 256
-// the 512 TMEM columns hold one accumulator and the scale factors.
+// buffers, starting as soon as the barriers exist; warp 1 (one lane)
+// issues tcgen05.mma into a TMEM accumulator and releases each stage with
+// tcgen05.commit; warps 2-9 write the scale factors into TMEM once, then
+// read the accumulator with tcgen05.ld (two warps per TMEM lane quarter,
+// alternate 32-column chunks), turn it into hit bits (S_jb = -len_j),
+// release it, and count the unsat clauses per column.  With N <= 128 there
+// are two accumulators and the next segment accumulates into the other
+// one meanwhile; above, the 512 TMEM columns hold one 256-column
+// accumulator and the scale factors, and the next segment waits only for
+// the bits to be read out.
 //
 // Schedule: with more tiles than SMs, every CTA of a one-per-SM grid takes
 // the same number of whole tiles, and when the leftover tiles would fill at
@@ -66,7 +69,8 @@ constexpr uint32_t kSfOne = 0x7F7F7F7Fu;  // four ue8m0 scale factors of 2^0
 constexpr int kStages = 4;
 constexpr int kAccBufs = 2;         // TMEM accumulators at most (segment j uses j % bufs)
 constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
-constexpr int kDenseThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kDenseThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per lane quarter)
+constexpr int kEpiWarps = 8;
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
 constexpr unsigned long long kWaitNs = 200ull * 1000ull * 1000ull;  // 200 ms
 // e2m1 codes (sign, 2 exponent bits with bias 1, 1 mantissa bit)
@@ -143,8 +147,11 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Named barrier of the four epilogue warps (128 threads).
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier of the eight epilogue warps (256 threads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Named barrier of the MMA and epilogue warps (warps 1-9, 288 threads).
+__device__ __forceinline__ void roles_sync() { asm volatile("bar.sync 2, 288;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             unsigned long long *bar) {
@@ -222,6 +229,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Issues a load of 32 consecutive columns of the warp's 32 TMEM lanes;
+// the registers hold the data only after tmem_wait2 below.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+// Waits for the warp's outstanding TMEM loads; a and b are tied to the
+// wait so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait2(uint32_t (&a)[32], uint32_t (&b)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]), "+r"(a[18]), "+r"(a[19]), "+r"(a[20]), "+r"(a[21]), "+r"(a[22]), "+r"(a[23]), "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]), "+r"(a[28]), "+r"(a[29]), "+r"(a[30]), "+r"(a[31]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(b[16]), "+r"(b[17]), "+r"(b[18]), "+r"(b[19]), "+r"(b[20]), "+r"(b[21]), "+r"(b[22]), "+r"(b[23]), "+r"(b[24]), "+r"(b[25]), "+r"(b[26]), "+r"(b[27]), "+r"(b[28]), "+r"(b[29]), "+r"(b[30]), "+r"(b[31])
+                 :
+                 : "memory");
+}
+
 // Writes v into 32 consecutive columns of the warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
     asm volatile(
@@ -233,6 +259,39 @@ __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// Column sums of a 32 x 32 block held one row per lane (x[c] of lane r is
+// entry (r, c)): five butterfly rounds, each lane trading half of its
+// remaining columns with lane ^ k and adding the other half's partners;
+// afterwards lane l holds the sum of column l.  Integer adds, so exact;
+// the caller keeps every column sum below 2^32 (32 weights below 2^25).
+__device__ __forceinline__ uint32_t column_sums32(uint32_t (&x)[32], int lane) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int i = 0; i < k; ++i) {
+            const uint32_t send = up ? x[i] : x[i + k];
+            const uint32_t keep = up ? x[i + k] : x[i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+    return x[0];
+}
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane
+// r's word is entry (r, c)): five butterfly rounds, each exchanging with
+// lane ^ j the half of the bits whose position has bit j set; afterwards
+// bit r of lane l's word is entry (r, l).
+__device__ __forceinline__ uint32_t transpose_bits32(uint32_t x, int lane) {
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1, m ^= m << j) {
+        const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (((t >> j) & m) | (x & ~m)) : ((x & m) | ((t & m) << j));
+    }
+    return x;
+}
+
 // One segment of a CTA's work: k-steps [ka, kb) of tile `tile`; tr is the
 // split-tile index (-1 for a whole tile) and piece the part of it.
 struct DenseSeg {
@@ -240,12 +299,17 @@ struct DenseSeg {
 };
 
 __device__ __forceinline__ int seg_count(const DenseSched &d, int c) {
-    return d.full + (c < d.tail_ctas ? 1 : 0);
+    return d.full + (c < d.tail_ctas || c < d.extra ? 1 : 0);
 }
 
+// A CTA with a piece of a split tile takes the piece first: the piece's
+// bookkeeping (bits stored, counted in, the last piece's combine) then
+// overlaps the CTA's whole tiles instead of ending the launch.
 __device__ __forceinline__ DenseSeg seg_at(const DenseSched &d, int c, int j) {
     DenseSeg g;
-    if (j < d.full) {
+    const bool piece_first = c < d.tail_ctas;
+    if (!piece_first || j > 0) {
+        if (piece_first) --j;
         g.tile = j * (int)gridDim.x + c;
         g.ka = 0;
         g.kb = d.kt_count;
@@ -263,7 +327,7 @@ __device__ __forceinline__ DenseSeg seg_at(const DenseSched &d, int c, int j) {
 
 __global__ void __launch_bounds__(kDenseThreads, 1)
     k_dense_eval(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const float *__restrict__ target, const uint32_t *__restrict__ wgt, DenseSched d,
+                 const float *__restrict__ target, const uint32_t *__restrict__ wgt, int unit_w, DenseSched d,
                  int tmem_cols, int nb, unsigned long long *__restrict__ cost, const float *__restrict__ ptgt,
                  uint32_t *__restrict__ pmask, unsigned int *__restrict__ part_cnt,
                  unsigned int *__restrict__ errflag) {
@@ -288,7 +352,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         }
         for (int b = 0; b < nbuf; ++b) {
             mbar_init(&H->acc_full[b], 1);
-            mbar_init(&H->acc_empty[b], 4);  // one arrive per epilogue warp
+            mbar_init(&H->acc_empty[b], kEpiWarps);  // one arrive per epilogue warp
         }
         mbar_init(&H->drain, 1);
         H->abort = 0;
@@ -297,23 +361,30 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int c = threadIdx.x; c < 256; c += blockDim.x) H->colsum[c] = 0ull;
-    if (warp == 1) {  // all 512 columns (one CTA per SM)
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&H->tmem)),
-                     "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = H->tmem;
+    __syncthreads();  // barriers initialised: the producer may start
     const int nseg = seg_count(d, cta);
-    // scale factors 2^0 in every byte of the scale-factor columns, written
-    // before the first MMA is issued
-    if (warp >= 2) tmem_fill32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)sf_col, kSfOne);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    uint32_t tmem = 0;
+    if (warp >= 1) {
+        // while the first loads are in flight: warps 1-5 allocate TMEM
+        // (all 512 columns, one CTA per SM) and write the scale factors,
+        // 2^0 in every byte of the scale-factor columns, before the first
+        // MMA is issued
+        if (warp == 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&H->tmem)),
+                         "r"(512)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tc_fence_before();
+        roles_sync();
+        tc_fence_after();
+        tmem = H->tmem;
+        if (warp >= 2 && warp < 6) tmem_fill32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)sf_col, kSfOne);
+        tc_fence_before();
+        roles_sync();
+        tc_fence_after();
+    }
 
     if (warp == 0 && lane == 0) {
         // producer: TMA loads of the A (clause rows) and B (assignment rows)
@@ -396,8 +467,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         }
     } else if (warp >= 2) {
         // epilogue: TMEM lane quarter q (= warp % 4) holds clause rows
-        // m0 + 32q .. + 31 of the segment's tile
+        // m0 + 32q .. + 31 of the segment's tile; of the two warps of a
+        // quarter, half h takes the 32-column chunks 2 i + h
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         const int r = 32 * q + lane;  // row within the tile
         const int etid = threadIdx.x - 64;
         for (int j = 0; j < nseg; ++j) {
@@ -406,86 +479,110 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             const bool ok = mbar_wait_abort(&H->acc_full[buf], (uint32_t)((j / nbuf) & 1), &H->abort);
             if (!ok) H->epi_fail = 1;
             epi_sync();
-            if (H->epi_fail) {  // the same decision in all four warps
+            if (H->epi_fail) {  // the same decision in all eight warps
                 if (etid == 0) atomicOr(errflag, 4u);
                 H->abort = 1;
                 break;
             }
             tc_fence_after();
             const int m0 = (g.tile % d.tiles_m) * kTM, n0 = (g.tile / d.tiles_m) * ntile;
-            const float tgt = __ldg(target + m0 + r);
             const uint32_t w = __ldg(wgt + m0 + r);
             const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * tmem_cols);
+            const int nch = (ntile + 31) / 32;
+            // the accumulator as hit masks: bit c of hm[ch] says that
+            // column 32 ch + c of the row reached its target -- -len_j for
+            // a whole tile (the clause is unsat), the piece's target for a
+            // piece of a split tile (every literal of the clause in the
+            // piece's k-range is false); columns past ntile never hit
+            size_t slot = 0;
+            float cmp;
             if (g.tr < 0) {
-                // a whole tile: the sums are complete; count the unsat
-                // clauses per column
-                for (int c0 = 0; c0 < ntile; c0 += 32) {
-                    uint32_t v[32];
-                    tmem_ld32(acc + (uint32_t)c0, v);
-                    uint32_t mine = 0;
+                cmp = __ldg(target + m0 + r);
+            } else {
+                slot = (size_t)g.tr * d.split + g.piece;
+                cmp = __ldg(ptgt + slot * kTM + r);
+            }
+            // this half's chunks 2 i + h, two 32-column loads in flight
+            // per wait
+            uint32_t hm[4];
+#pragma unroll
+            for (int i = 0; i < 4; i += 2) {
+                const int c0 = 2 * i + h, c1 = c0 + 2;
+                hm[i] = hm[i + 1] = 0u;
+                if (c0 < nch) {
+                    uint32_t va[32], vb[32];
+                    tmem_ld32_issue(acc + (uint32_t)(32 * c0), va);
+                    // past the last chunk: the same columns again (dropped below)
+                    tmem_ld32_issue(acc + (uint32_t)(32 * (c1 < nch ? c1 : c0)), vb);
+                    tmem_wait2(va, vb);
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
-                        const uint32_t hit = (__uint_as_float(v[c]) == tgt) ? w : 0u;
-                        const uint32_t sum = __reduce_add_sync(0xffffffffu, hit);
-                        if (lane == c) mine = sum;
-                    }
-                    if (mine) atomicAdd(&H->colsum[c0 + lane], (unsigned long long)mine);
-                }
-            } else {
-                // a piece of a split tile: bit c of word [chunk][row] says
-                // that every literal of the row's clause in this piece's
-                // k-range is false under assignment chunk * 32 + c
-                const int nch = (ntile + 31) / 32;  // columns past ntile are never flushed
-                const size_t slot = (size_t)g.tr * d.split + g.piece;
-                const float ptg = __ldg(ptgt + slot * kTM + r);
-                uint32_t bits[8];
-#pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    bits[ch] = 0u;
-                    if (ch < nch) {
-                        uint32_t v[32];
-                        tmem_ld32(acc + (uint32_t)(32 * ch), v);
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) bits[ch] |= (__uint_as_float(v[c]) == ptg ? 1u : 0u) << c;
-                        pmask[(slot * nch + ch) * kTM + r] = bits[ch];
+                        hm[i] |= (__uint_as_float(va[c]) == cmp ? 1u : 0u) << c;
+                        hm[i + 1] |= (__uint_as_float(vb[c]) == cmp ? 1u : 0u) << c;
                     }
                 }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int live = ntile - 32 * (2 * i + h);
+                if (live <= 0) hm[i] = 0u;
+                else if (live < 32) hm[i] &= (1u << live) - 1u;
+            }
+            // every column is read: the accumulator buffer is free for
+            // segment j + nbuf while this one is counted
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&H->acc_empty[buf]);
+            bool count = true;
+            if (g.tr >= 0) {
+                // a piece of a split tile: store the bits, count this
+                // piece in; the last piece of the tile ANDs the others'
+                // bits into its own and counts the tile
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (2 * i + h < nch) pmask[(slot * nch + 2 * i + h) * kTM + r] = hm[i];
                 __threadfence();  // this CTA's bits before its count
                 epi_sync();
                 if (etid == 0) H->last = atomicAdd(part_cnt + g.tr, 1u) == (unsigned)(d.split - 1);
                 epi_sync();
-                if (H->last) {
+                count = H->last != 0;
+                if (count) {
                     __threadfence();
                     for (int pc = 0; pc < d.split; ++pc) {
                         if (pc == g.piece) continue;
                         const uint32_t *other = pmask + ((size_t)g.tr * d.split + pc) * nch * kTM + r;
 #pragma unroll
-                        for (int ch = 0; ch < 8; ++ch)
-                            if (ch < nch) bits[ch] &= __ldcg(other + (size_t)ch * kTM);
-                    }
-#pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
-                        if (ch < nch) {
-                            uint32_t mine = 0;
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                const uint32_t hit = ((bits[ch] >> c) & 1u) ? w : 0u;
-                                const uint32_t hs = __reduce_add_sync(0xffffffffu, hit);
-                                if (lane == c) mine = hs;
-                            }
-                            if (mine) atomicAdd(&H->colsum[32 * ch + lane], (unsigned long long)mine);
-                        }
+                        for (int i = 0; i < 4; ++i)
+                            if (2 * i + h < nch) hm[i] &= __ldcg(other + (size_t)(2 * i + h) * kTM);
                     }
                     if (etid == 0) part_cnt[g.tr] = 0u;  // ready for the next launch
                 }
             }
-            // the accumulator buffer is free for segment j + nbuf
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&H->acc_empty[buf]);
+            if (count) {
+                // unsat count per column over the warp's 32 rows (lane l
+                // gets column l), then added over the four quarters: with unit
+                // weights the popcount of the transposed hit bits, else
+                // the column sums of w [hit]
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ch = 2 * i + h;
+                    if (ch < nch && __any_sync(0xffffffffu, hm[i] != 0u)) {
+                        uint32_t sum;
+                        if (unit_w) {
+                            sum = (uint32_t)__popc(transpose_bits32(hm[i], lane));
+                        } else {
+                            uint32_t x[32];
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) x[c] = ((hm[i] >> c) & 1u) ? w : 0u;
+                            sum = column_sums32(x, lane);
+                        }
+                        if (sum) atomicAdd(&H->colsum[32 * ch + lane], (unsigned long long)sum);
+                    }
+                }
+            }
             // add the tile's column sums to the costs
             epi_sync();
-            for (int cc = etid; cc < ntile; cc += 128) {
+            for (int cc = etid; cc < ntile; cc += 32 * kEpiWarps) {
                 const unsigned long long cs = H->colsum[cc];
                 if (cs) {
                     if (n0 + cc < nb) atomicAdd(cost + n0 + cc, cs);
@@ -514,6 +611,62 @@ __global__ void k_wait_selftest(long long spins, unsigned int *errflag) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (!mbar_wait(&bar, 0u, spins, kWaitNs)) atomicOr(errflag, 8u);
     }
+}
+
+// Issue rate of the evaluator's MMA on its own: one CTA per SM issues
+// `iters` stages of four kind::mxf4 MMAs (M = 128, N = n, K = 64 codes
+// each) on operands resident in shared memory (zero codes, unit scale
+// factors), cycling over four stage buffers like the pipeline does, and
+// waits (bounded) for them to complete.  The host times the launch: the
+// measured peak of this instruction shape, which the evaluator's pipeline
+// can approach but not pass.
+__global__ void __launch_bounds__(128, 1) k_mma_rate(int n, int iters, unsigned int *__restrict__ errflag) {
+    extern __shared__ uint8_t dsm_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint32_t tmem_s;
+    __shared__ __align__(8) unsigned long long done;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t stage_bytes = (uint32_t)(kTM + n) * kRowBytes;
+    for (uint32_t i = threadIdx.x; i < kStages * stage_bytes / 4; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(base)[i] = 0u;
+    if (threadIdx.x == 0) {
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_s;
+    const uint32_t sf_col = 256;
+    tmem_fill32(tmem + ((uint32_t)(32 * warp) << 16) + sf_col, kSfOne);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeros, for the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = idesc_mxf4(n);
+        for (int it = 0; it < iters; ++it) {
+            const uint32_t sa = smem_u32(base + (size_t)(it % kStages) * stage_bytes);
+            const uint64_t adesc = smem_desc_sw128(sa);
+            const uint64_t bdesc = smem_desc_sw128(sa + kTM * kRowBytes);
+#pragma unroll
+            for (int kk = 0; kk < kRowBytes / 32; ++kk)
+                mma_mxf4(tmem, adesc + 2 * kk, bdesc + 2 * kk, idesc, tmem + sf_col, tmem + sf_col + kSfCols / 2,
+                         (it != 0 || kk != 0) ? 1u : 0u);
+        }
+        mma_commit(&done);
+        if (!mbar_wait(&done, 0u, 0, kWaitNs)) atomicOr(errflag, 32u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // Per-piece targets of the split tiles: for split tile tr, piece p and row
@@ -696,10 +849,12 @@ cudaError_t launch_dense_convert_x(const DenseDev &d, const float *x, int n, int
     return cudaGetLastError();
 }
 
-// Whole tiles one per CTA when they fit one wave of one CTA per SM; with
-// more tiles, equal whole-tile shares per CTA, and a leftover of at most
-// half a wave split into up to 4 k-step pieces per tile (a larger leftover
-// runs as a last partial wave of whole tiles).
+// Whole tiles one per CTA when they fit one wave of one CTA per SM.  With
+// more tiles the grid stays one CTA per SM and each CTA streams its tiles
+// back to back (the next tile's loads overlap the last one's epilogue):
+// equal whole-tile shares, then a leftover of at most half a wave split
+// into up to 4 k-step pieces per tile, or a larger leftover as one more
+// whole tile on the first CTAs.
 DenseSched dense_plan(const DenseDev &d, int ntile, int *grid) {
     DenseSched p{};
     p.kt_count = d.n_pad / kTK;
@@ -715,12 +870,14 @@ DenseSched dense_plan(const DenseDev &d, int ntile, int *grid) {
         int split = rest > 0 ? G / rest : 0;
         if (split > 4) split = 4;
         if (split > p.kt_count) split = p.kt_count;
+        p.full = full;
+        *grid = G;
         if (rest > 0 && split >= 2) {
-            p.full = full;
             p.tail = rest;
             p.split = split;
             p.tail_ctas = rest * split;
-            *grid = G;
+        } else {
+            p.extra = rest;
         }
     }
     return p;
@@ -738,9 +895,9 @@ cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaSt
     const DenseSched p = dense_plan(d, ntile, &grid);
     if (p.tail > 0 && (p.tail * p.split > d.ptgt_slots || p.tail > d.part_cnts || ntile != d.pmask_ntile))
         return cudaErrorInvalidValue;
-    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, p, tmem_cols, nb,
-                                                   reinterpret_cast<unsigned long long *>(cost), d.ptgt, d.pmask,
-                                                   d.part_cnt, d.errflag);
+    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, d.unit_w ? 1 : 0, p, tmem_cols,
+                                                   nb, reinterpret_cast<unsigned long long *>(cost), d.ptgt,
+                                                   d.pmask, d.part_cnt, d.errflag);
     return cudaGetLastError();
 }
 
@@ -750,6 +907,14 @@ cudaError_t launch_dense_piece_targets(const DevInst &I, const DenseDev &d, cons
                                        cudaStream_t st) {
     if (p.tail <= 0) return cudaSuccess;
     k_dense_piece_targets<<<p.tail, kTM, 0, st>>>(I, d.target, p, grid, d.ptgt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mma_rate(int n, int iters, int grid, unsigned int *errflag, cudaStream_t st) {
+    const size_t smem = 1024 + (size_t)kStages * (kTM + n) * kRowBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_mma_rate<<<grid, 128, smem, st>>>(n, iters, errflag);
     return cudaGetLastError();
 }
 

@@ -105,14 +105,16 @@ struct DevState {
 // [m_pad][n_pad] in packed e2m1 (n_pad / 2 bytes a row), per-row target
 // -len_j (NaN: never unsat), 32-bit weights, the packed e2m1 assignment
 // batch X^T [rows][n_pad] and their TMA descriptors.
-// Work split of one dense launch: tile t covers clause rows
-// (t % tiles_m) * 128 and assignment columns (t / tiles_m) * ntile; CTA c
-// takes whole tiles j * grid + c for j < full, then (c < tail_ctas) piece
-// c % split of split tile c / split: k-steps [piece * kt_count / split,
-// (piece + 1) * kt_count / split) of tile full * grid + c / split.
 // Variables per k-step of the dense evaluation (n is padded to a multiple).
 constexpr int kDenseKStep = 256;
 
+// Work split of one dense launch: tile t covers clause rows
+// (t % tiles_m) * 128 and assignment columns (t / tiles_m) * ntile; CTA c
+// takes whole tiles j * grid + c for j < full, then (c < extra) whole tile
+// full * grid + c, or (c < tail_ctas) piece c % split of split tile
+// c / split: k-steps [piece * kt_count / split, (piece + 1) * kt_count /
+// split) of tile full * grid + c / split.  extra and tail are never both
+// nonzero.
 struct DenseSched {
     int kt_count;   // k-steps (kDenseKStep variables) per tile
     int tiles_m;
@@ -121,12 +123,14 @@ struct DenseSched {
     int tail;       // split tiles
     int split;      // pieces per split tile
     int tail_ctas;  // tail * split
+    int extra;      // CTAs that take one more whole tile
 };
 
 struct DenseDev {
     uint8_t *Wt = nullptr;
     float *target = nullptr;
     uint32_t *wgt = nullptr;
+    bool unit_w = false;  // every clause weight is 1
     int m_pad = 0, n_pad = 0;
     uint8_t *Xt = nullptr;
     size_t xt_bytes = 0;
@@ -311,5 +315,7 @@ cudaError_t launch_dense_piece_targets(const DevInst &I, const DenseDev &d, cons
                                        cudaStream_t st);
 cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaStream_t st);
 cudaError_t launch_wait_selftest(long long spins, unsigned int *errflag, cudaStream_t st);
+// k_mma_rate: `iters` stages of four MMAs of the evaluator's shape, N = n.
+cudaError_t launch_mma_rate(int n, int iters, int grid, unsigned int *errflag, cudaStream_t st);
 
 }  // namespace msat

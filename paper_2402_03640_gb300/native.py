@@ -143,6 +143,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "msat_autotune": ([i32, i64, P, P, P, P, P, i32, P, P, i32, P], ctypes.c_int),
             "msat_heuristic_gap": ([P, P, P], ctypes.c_int),
             "msat_selftest_bounded_wait": ([i64], ctypes.c_int),
+            "msat_dense_mma_rate": ([i32, i32, P], ctypes.c_int),
             "msat_best_step": ([P, P], ctypes.c_int),
             "msat_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
             "msat_profile_read": ([P, P, ctypes.c_int], ctypes.c_int),

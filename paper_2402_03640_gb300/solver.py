@@ -404,3 +404,11 @@ def msat_loss(x, solver: Solver):
     if _MsatLoss is None:
         _MsatLoss = _make_autograd()
     return _MsatLoss.apply(x, solver)
+
+
+def dense_mma_rate(n_assign: int = 256, iters: int = 4096) -> float:
+    """TFLOP/s of the dense backend's MMA instruction shape issued back to
+    back on every SM with operands resident in shared memory (msat_dense_mma_rate)."""
+    out = ctypes.c_double(0.0)
+    native.check(native.load().msat_dense_mma_rate(int(n_assign), int(iters), ctypes.byref(out)))
+    return out.value

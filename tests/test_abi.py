@@ -101,6 +101,10 @@ def test_null_arguments(lib):
     assert lib.msat_heuristic_gap(None, None, None) == native.MSAT_EINVAL
     assert lib.msat_selftest_bounded_wait(-1) == native.MSAT_EINVAL
     assert lib.msat_selftest_bounded_wait((1 << 24) + 1) == native.MSAT_EINVAL
+    out = ctypes.c_double(0.0)
+    assert lib.msat_dense_mma_rate(256, 16, None) == native.MSAT_EINVAL
+    for n_assign, iters in ((0, 16), (24, 16), (272, 16), (256, 0), (256, (1 << 20) + 1)):
+        assert lib.msat_dense_mma_rate(n_assign, iters, ctypes.byref(out)) == native.MSAT_EINVAL
     assert lib.msat_best_step(None, None) == native.MSAT_EINVAL
     assert lib.msat_autotune(1, 0, None, None, None, None, None, 1, None, None, 0, None) == native.MSAT_EINVAL
     lib.msat_destroy(None)

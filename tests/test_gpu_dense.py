@@ -99,11 +99,27 @@ def test_evaluate_current_x_both_backends(pkg, oracle):
     assert np.array_equal(d, cost) and np.array_equal(sp, cost)
 
 
-@pytest.mark.parametrize("m,nbs", [(19500, [64, 256]), (25000, [16, 200]), (40000, [300])])
+@pytest.mark.parametrize("m,nbs", [(19500, [64, 256]), (25000, [16, 200]), (40000, [300]),
+                                   (38912, [256, 32]), (32256, [64])])
 def test_dense_tile_counts_past_one_wave(pkg, oracle, m, nbs):
-    """Clause-tile counts just above one wave of SMs (a small leftover split
-    into k-step pieces), between one and two waves and above two (whole
-    tiles in a last partial wave; two assignment tiles for 300
-    assignments)."""
+    """Clause-tile counts on a persistent grid of one CTA per SM (152 SMs):
+    just above one wave (a small leftover split into k-step pieces),
+    between one and two waves, above two with two assignment tiles (300
+    assignments), exactly two waves (304 tiles, no leftover), and a
+    leftover of more than half a wave (252 tiles: 100 CTAs take one more
+    whole tile)."""
     cnf = uniform_ksat(3000, m, 3, seed=m)
     _check(pkg, oracle, cnf, nbs, seed=m)
+
+
+@pytest.mark.gpu
+def test_dense_mma_rate_is_a_plausible_peak(pkg):
+    """The measured rate of the evaluator's MMA shape: positive, no waits
+    given up, and N = 256 at least as fast in flops as N = 64 (the wider
+    MMA does more work per instruction); the device stays usable."""
+    r256 = pkg.dense_mma_rate(256, 2048)
+    r64 = pkg.dense_mma_rate(64, 2048)
+    assert r256 > 100.0 and r64 > 10.0
+    assert r256 >= 0.9 * r64
+    import torch
+    assert int(torch.ones(4, device="cuda").sum().item()) == 4
