@@ -996,8 +996,10 @@ def run_serving(args):
     return 0
 
 
-KERNEL_SOURCES = {"forward": ("k_step.cu", "msat_internal.cuh"),
-                  "backward": ("k_step.cu", "msat_internal.cuh"),
+# a kernel's sources and those of the data layout it reads (host_cnf.cu
+# builds the row order of the stored w f)
+KERNEL_SOURCES = {"forward": ("k_step.cu", "msat_internal.cuh", "host_cnf.cu"),
+                  "backward": ("k_step.cu", "msat_internal.cuh", "host_cnf.cu"),
                   "dense_eval": ("k_dense.cu", "msat_internal.cuh"),
                   "small_steps": ("k_step.cu", "msat_internal.cuh")}
 
