@@ -712,7 +712,7 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    unsigned long long my_tot = 0;  // this thread's share of sum_b cost_b
+    unsigned long long my_tot = 0;  // this thread's restarts' costs
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         // every block's additions are complete (fence before the counter):
         // read the replicas from L2, then clear them for the next pass
@@ -739,17 +739,15 @@ __device__ __forceinline__ void forward_body(const DevInst &I, const float *__re
         const float den = ln == 1 ? 1.0f : (float)(ln == 2 ? D.sc->wsum : c);
         D.cscale[b] = c > 0 ? 2.0f / den : 0.0f;
     }
-    // sum of the costs over the restarts: warp sums, then thread 0 adds the
-    // warps' (integers: any order is exact)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_tot += __shfl_xor_sync(0xffffffffu, my_tot, o);
-    if (lane == 0) s_w[threadIdx.x >> 5] = my_tot;
+    // the sum over the restarts from shared memory (integers: any order is
+    // exact); the costs just written to global memory are not read back
+    s_w[threadIdx.x] = my_tot;
     __syncthreads();
     if (threadIdx.x == 0) {
         StepScalars *sc = D.sc;
         sc->counter = 0;
         unsigned long long tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_w[w];
+        for (int k = 0; k < (int)blockDim.x; ++k) tot += s_w[k];
         sc->dense = (double)tot * 16.0 > (double)sc->wsum * (double)B;
         if (mode == FWD_STEP) {
             const double p1 = sc->p1 * sc->beta1;
