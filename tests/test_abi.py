@@ -83,6 +83,9 @@ def _create(lib, n, off, lits, w=None, restarts=1, **shape):
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=1024, fwd_vw=2), "must not exceed 256"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=512, stage_vw=1), "must not exceed 256"),
     (dict(n=2, off=[0, 2], lits=[1, 2], restarts=4, fwd_vw=8), "powers of two"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], loss_norm=7), "unknown loss_norm"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], row_order=3), "unknown row_order"),
+    (dict(n=2, off=[0, 2], lits=[1, 2], row_order=-1), "unknown row_order"),
 ])
 def test_create_rejects_malformed_input(lib, case, needle):
     from paper_2402_03640_gb300 import native
