@@ -293,7 +293,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     const int64_t nB = (int64_t)n_vars * B;
     int rc = MSAT_OK;
     int32_t *d_coff = nullptr, *d_lit = nullptr, *d_voff = nullptr, *d_occ = nullptr;
-    int32_t *d_hvar = nullptr, *d_hch = nullptr;
+    int32_t *d_hvar = nullptr, *d_hch = nullptr, *d_hofc = nullptr;
     int2 *d_lblk = nullptr, *d_occx = nullptr;
     int32_t *d_plit = nullptr, *d_pcoff = nullptr;
     int64_t *d_pw = nullptr;
@@ -310,6 +310,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     TRY_ALLOC(d_occ, nnz);
     TRY_ALLOC(d_hvar, (int64_t)hvar.size());
     TRY_ALLOC(d_hch, (int64_t)hchunk0.size());
+    TRY_ALLOC(d_hofc, std::max<int64_t>(1, hchunk0.back()));
     TRY_ALLOC(d_lblk, (int64_t)lblk.size());
     if (expand) TRY_ALLOC(d_occx, nnz);
     if (block_rows) {
@@ -341,6 +342,7 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     I.heavy_chunks = hchunk0.back();
     I.heavy_var = d_hvar;
     I.heavy_chunk0 = d_hch;
+    I.heavy_of_chunk = d_hofc;
     I.occ_shift = expand ? 3 : 1;
     I.occx = d_occx;
     I.n_lblk = (int32_t)lblk.size();
@@ -398,6 +400,11 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (!e) e = up(d_occ, occ.data(), sizeof(int32_t) * occ.size());
     if (!e) e = up(d_hvar, hvar.data(), sizeof(int32_t) * hvar.size());
     if (!e) e = up(d_hch, hchunk0.data(), sizeof(int32_t) * hchunk0.size());
+    // the heavy variable of every chunk (one load per chunk block)
+    std::vector<int32_t> hofc((size_t)std::max<int32_t>(1, hchunk0.back()), 0);
+    for (size_t h = 0; h + 1 < hchunk0.size(); ++h)
+        for (int32_t ch = hchunk0[h]; ch < hchunk0[h + 1]; ++ch) hofc[(size_t)ch] = (int32_t)h;
+    if (!e) e = up(d_hofc, hofc.data(), sizeof(int32_t) * hofc.size());
     if (!e) e = up(d_lblk, lblk.data(), sizeof(int2) * lblk.size());
     if (!e && expand) e = up(d_occx, occx.data(), sizeof(int2) * occx.size());
     if (!e && block_rows) e = up(d_plit, ro.plit.data(), sizeof(int32_t) * ro.plit.size());

@@ -888,12 +888,7 @@ __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, 
     const int gg = blk % G;
     const long long cidx = blk / G;
     const int col = gg * VW;
-    int lo = 0, hi = I.n_heavy - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(I.heavy_chunk0 + mid) <= cidx) lo = mid; else hi = mid - 1;
-    }
-    const int h = lo;
+    const int h = __ldg(I.heavy_of_chunk + cidx);
     const int i = __ldg(I.heavy_var + h);
     const int c0 = __ldg(I.heavy_chunk0 + h);
     const int nch = __ldg(I.heavy_chunk0 + h + 1) - c0;
@@ -937,6 +932,7 @@ __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, 
 #pragma unroll
             for (int e = 0; e < VW; ++e) leaf[e] = 0.0f;
             const int lb = lane * 32, le = min(lb + 32, cn);
+#pragma unroll 8
             for (int r = lb; r < le; ++r)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) leaf[e] = (r == lb) ? s_term[r * VW + e] : leaf[e] + s_term[r * VW + e];
@@ -949,10 +945,11 @@ __device__ __forceinline__ void heavy_body(const DevInst &I, const DevState &S, 
             }
         }
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0)
+    // thread 0 wrote the chunk's partial: it alone fences before counting in
+    if (threadIdx.x == 0) {
+        __threadfence();
         s_last = (atomicAdd(D.hcount + (long long)h * G + gg, 1u) == (unsigned)(nch - 1));
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();

@@ -44,6 +44,7 @@ struct DevInst {
     long long heavy_chunks;       // total chunks of the heavy variables
     const int32_t *heavy_var;     // [n_heavy] variable ids
     const int32_t *heavy_chunk0;  // [n_heavy+1] prefix of chunk counts
+    const int32_t *heavy_of_chunk;  // [heavy_chunks] heavy index h of each chunk
     int32_t occ_shift;            // occ word: clause index above this bit (1, or 3 when
                                   // bits 1-2 hold the variable's position in its clause)
     const int2 *occx;             // [nnz] other two literals of a 3-literal clause, or nullptr
