@@ -1179,19 +1179,41 @@ __global__ void __launch_bounds__(kThreads, 4)
     vars_body<VS, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x, gridDim.x);
 }
 
+// Heavy-variable chunks and light blocks in one launch: blocks [0, hblocks)
+// take the chunks (first, so the long variables start early), the rest the
+// light blocks.  The two write disjoint variables, so neither waits for the
+// other, and each fills the other's last partial wave.
+template <int VS, int VU, int KFIX, bool STORE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_backward_mixed(DevInst I, DevState S, DevStep D, int mode, const float *__restrict__ t_ovr,
+                     const float *__restrict__ gscale, float *__restrict__ grad_out, int hblocks,
+                     int lblocks) {
+    if ((int)blockIdx.x < hblocks)
+        heavy_body<VU, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, blockIdx.x);
+    else
+        vars_body<VS, KFIX, STORE>(I, S, D, mode, t_ovr, gscale, grad_out, (int)blockIdx.x - hblocks, lblocks);
+}
+
 template <int VS, int VU, int KFIX, bool STORE>
 static cudaError_t launch_backward_k(const DevInst &I, const DevState &S, const DevStep &D,
                                      int mode, const float *t_ovr, const float *gscale,
                                      float *grad_out, cudaStream_t st) {
+    const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
+    const size_t smem = light_smem_bytes(I.task_cap, VS);
     if (I.n_heavy > 0) {
         const long long hblocks = I.heavy_chunks * (I.B / VU);  // one block per (chunk, group)
+        if constexpr (STORE && VU <= 2 && VS <= 2) {
+            // one launch where that keeps the light blocks' 64-register,
+            // four-blocks-per-SM shape without spills
+            k_backward_mixed<VS, VU, KFIX, STORE, 4><<<(unsigned)(hblocks + lblocks), kThreads, smem, st>>>(
+                I, S, D, mode, t_ovr, gscale, grad_out, (int)hblocks, (int)lblocks);
+            return cudaGetLastError();
+        }
         k_backward_heavy<VU, KFIX, STORE><<<(unsigned)hblocks, kThreads, 0, st>>>(I, S, D, mode, t_ovr,
                                                                                    gscale, grad_out);
         const cudaError_t e = cudaGetLastError();
         if (e) return e;
     }
-    const long long lblocks = I.n_lblk > 0 ? I.n_lblk : 1;
-    const size_t smem = light_smem_bytes(I.task_cap, VS);
     if constexpr ((STORE && VS <= 4) || VS <= 2)
         k_backward_light_occ4<VS, KFIX, STORE><<<(unsigned)lblocks, kThreads, smem, st>>>(I, S, D, mode, t_ovr,
                                                                                       gscale, grad_out);
