@@ -173,23 +173,55 @@ __device__ __forceinline__ void clause_value(const DevInst &I, const float *__re
     float stk[kClauseLevels][VW];
     unsigned nleaf = 0;
     int in_leaf = 0;
-#pragma unroll 2
-    for (int p = beg; p < end; ++p) {
-        if (in_leaf == 32) {
-            leaf_push<VW>(stk, nleaf, f);
-            in_leaf = 0;
-        }
-        const int L = __ldg(I.lit + p);
-        const bool neg = L & 1;
-        float tv[VW];
-        ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
+    if constexpr (WANT_SAT && VW <= 2) {
+        // the clause pass with one or two restarts a thread: NB literals at
+        // a time -- their loads, then their row gathers, then the terms in
+        // literal order (the same additions as one literal at a time)
+        constexpr int NB = 8 / VW;
+        for (int p0 = beg; p0 < end; p0 += NB) {
+            int L[NB];
+            float tv[NB][VW];
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const float term = neg ? -tv[e] : tv[e];
-            f[e] = (in_leaf == 0) ? term : f[e] + term;
-            if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
+            for (int k = 0; k < NB; ++k) L[k] = p0 + k < end ? __ldg(I.lit + p0 + k) : 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (p0 + k < end) ldv<VW>(t + (int64_t)(L[k] >> 1) * B + col, tv[k]);
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                if (p0 + k >= end) break;
+                if (in_leaf == 32) {
+                    leaf_push<VW>(stk, nleaf, f);
+                    in_leaf = 0;
+                }
+                const bool neg = L[k] & 1;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const float term = neg ? -tv[k][e] : tv[k][e];
+                    f[e] = (in_leaf == 0) ? term : f[e] + term;
+                    sat[e] |= ((tv[k][e] > 0.0f) != neg);
+                }
+                ++in_leaf;
+            }
         }
-        ++in_leaf;
+    } else {
+#pragma unroll 2
+        for (int p = beg; p < end; ++p) {
+            if (in_leaf == 32) {
+                leaf_push<VW>(stk, nleaf, f);
+                in_leaf = 0;
+            }
+            const int L = __ldg(I.lit + p);
+            const bool neg = L & 1;
+            float tv[VW];
+            ldv<VW>(t + (int64_t)(L >> 1) * B + col, tv);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const float term = neg ? -tv[e] : tv[e];
+                f[e] = (in_leaf == 0) ? term : f[e] + term;
+                if (WANT_SAT) sat[e] |= ((tv[e] > 0.0f) != neg);
+            }
+            ++in_leaf;
+        }
     }
     if (nleaf) {  // more than 32 literals: the last leaf, then the counter
         leaf_push<VW>(stk, nleaf, f);
