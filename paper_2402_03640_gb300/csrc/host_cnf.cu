@@ -110,6 +110,8 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
         std::vector<int32_t> lit;
         int64_t wsum = 0;
         int32_t max_len = 0;
+        int32_t first_len = -1;  // length of the part's first clause
+        bool same_len = true;    // every clause of the part has first_len literals
         int64_t too_long = -1;
         std::vector<int32_t> seen, vseen;
     };
@@ -150,6 +152,8 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
                 }
             }
             const int32_t len = (int32_t)(P.lit.size() - start);
+            if (P.first_len < 0) P.first_len = len;
+            P.same_len = P.same_len && len == P.first_len;
             if (len > kMaxClauseLen && P.too_long < 0) P.too_long = j;
             P.max_len = std::max(P.max_len, len);
             out.clen[(size_t)j] = len;
@@ -184,13 +188,14 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
             out.coff[(size_t)j + 1] = (int32_t)at;
         }
     });
-    parts.clear();
+    // the common clause length (0 if the lengths differ), from the parts'
     out.kfix = 0;
     if (m > 0) {
         out.kfix = out.clen[0];
-        for (int64_t j = 1; j < m && out.kfix > 0; ++j)
-            if (out.clen[(size_t)j] != out.kfix) out.kfix = 0;
+        for (const Part &P : parts)
+            if (P.first_len >= 0 && (!P.same_len || P.first_len != out.kfix)) out.kfix = 0;
     }
+    parts.clear();
 
     // transposed CSR, stable: per-thread counts of each variable's
     // occurrences in the thread's clause range, turned into per-thread
@@ -203,22 +208,42 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
         std::fill(c, c + n, 0);
         for (int64_t p = out.coff[(size_t)b]; p < out.coff[(size_t)e]; ++p) ++c[out.lit[(size_t)p] >> 1];
     });
+    // occurrence offsets: the variables split into Tt ranges; each range's
+    // degrees and total, the ranges' starts in order, then each range's
+    // offsets and every thread's first slot per variable
     out.voff.alloc((size_t)n + 1);
-    int64_t acc = 0;
-    out.max_deg = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        out.voff[(size_t)i] = (int32_t)acc;
-        int64_t d = 0;
-        for (int t = 0; t < Tt; ++t) {
-            int32_t &c = cnt[(size_t)t * n + i];
-            const int32_t k = c;
-            c = (int32_t)(acc + d);  // thread t's first slot for variable i
-            d += k;
+    std::vector<int64_t> rtot((size_t)Tt + 1, 0);
+    std::vector<int32_t> rmax((size_t)Tt, 0);
+    parallel_ranges(n, Tt, [&](int r, int64_t b, int64_t e) {
+        int64_t tot = 0;
+        int32_t mx = 0;
+        for (int64_t i = b; i < e; ++i) {
+            int32_t d = 0;
+            for (int t = 0; t < Tt; ++t) d += cnt[(size_t)t * n + (size_t)i];
+            tot += d;
+            mx = std::max(mx, d);
         }
-        acc += d;
-        out.max_deg = std::max<int32_t>(out.max_deg, (int32_t)d);
+        rtot[(size_t)r + 1] = tot;
+        rmax[(size_t)r] = mx;
+    });
+    out.max_deg = 0;
+    for (int r = 0; r < Tt; ++r) {
+        rtot[(size_t)r + 1] += rtot[(size_t)r];
+        out.max_deg = std::max(out.max_deg, rmax[(size_t)r]);
     }
-    out.voff[(size_t)n] = (int32_t)acc;
+    parallel_ranges(n, Tt, [&](int r, int64_t b, int64_t e) {
+        int64_t acc = rtot[(size_t)r];
+        for (int64_t i = b; i < e; ++i) {
+            out.voff[(size_t)i] = (int32_t)acc;
+            for (int t = 0; t < Tt; ++t) {
+                int32_t &c = cnt[(size_t)t * n + (size_t)i];
+                const int32_t k = c;
+                c = (int32_t)acc;  // thread t's first slot for variable i
+                acc += k;
+            }
+        }
+    });
+    out.voff[(size_t)n] = (int32_t)rtot[(size_t)Tt];
     out.occ.alloc((size_t)out.nnz);
     parallel_ranges(m, Tt, [&](int t, int64_t b, int64_t e) {
         int32_t *c = cnt.get() + (size_t)t * n;
@@ -244,7 +269,8 @@ int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, con
     const int32_t nb = (int32_t)lblk.size();
     // home block of each clause: that of its first light variable (nb: none)
     ro.row.alloc((size_t)m);
-    std::vector<int32_t> home((size_t)m);
+    I32Buf home;
+    home.alloc((size_t)m);
     const int T = threads_for(m);
     std::vector<std::vector<int64_t>> cnt((size_t)T, std::vector<int64_t>((size_t)nb + 1, 0));
     parallel_ranges(m, T, [&](int t, int64_t b, int64_t e) {
@@ -275,22 +301,27 @@ int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, con
             cnt[(size_t)t][(size_t)h] = at;
             at += k;
         }
-    parallel_ranges(m, T, [&](int t, int64_t b, int64_t e) {
-        std::vector<int64_t> &c = cnt[(size_t)t];
-        for (int64_t j = b; j < e; ++j) ro.row[(size_t)j] = (int32_t)c[(size_t)home[(size_t)j]]++;
-    });
-    // the clause pass's arrays in row order
+    // each clause's row; with a common length the literals go to their row
+    // in the same pass, and the clause pass's arrays follow in row order
     const int64_t nnz = (int64_t)lit.size();
     ro.plit.alloc((size_t)nnz);
-    if (kfix > 0) {
+    parallel_ranges(m, T, [&](int t, int64_t b, int64_t e) {
+        std::vector<int64_t> &c = cnt[(size_t)t];
+        for (int64_t j = b; j < e; ++j) {
+            const int32_t r = (int32_t)c[(size_t)home[(size_t)j]]++;
+            ro.row[(size_t)j] = r;
+            if (kfix > 0)
+                for (int32_t p = 0; p < kfix; ++p)
+                    ro.plit[(size_t)r * kfix + p] = lit[(size_t)j * kfix + p];
+        }
+    });
+    if (kfix == 0) {
+        I32Buf len;
+        len.alloc((size_t)m);
         parallel_ranges(m, T, [&](int, int64_t b, int64_t e) {
             for (int64_t j = b; j < e; ++j)
-                for (int32_t p = 0; p < kfix; ++p)
-                    ro.plit[(size_t)ro.row[(size_t)j] * kfix + p] = lit[(size_t)j * kfix + p];
+                len[(size_t)ro.row[(size_t)j]] = coff[(size_t)j + 1] - coff[(size_t)j];
         });
-    } else {
-        std::vector<int32_t> len((size_t)m);
-        for (int64_t j = 0; j < m; ++j) len[(size_t)ro.row[(size_t)j]] = coff[(size_t)j + 1] - coff[(size_t)j];
         ro.pcoff.alloc((size_t)m + 1);
         ro.pcoff[0] = 0;
         for (int64_t r = 0; r < m; ++r) ro.pcoff[(size_t)r + 1] = ro.pcoff[(size_t)r] + len[(size_t)r];
@@ -302,8 +333,10 @@ int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, con
         });
     }
     if (w) {
-        ro.pw.assign((size_t)m, 0);
-        for (int64_t j = 0; j < m; ++j) ro.pw[(size_t)ro.row[(size_t)j]] = w[j];
+        ro.pw.resize((size_t)m);
+        parallel_ranges(m, T, [&](int, int64_t b, int64_t e) {
+            for (int64_t j = b; j < e; ++j) ro.pw[(size_t)ro.row[(size_t)j]] = w[j];
+        });
     }
     return MSAT_OK;
 }
