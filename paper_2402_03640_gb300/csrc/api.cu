@@ -255,8 +255,8 @@ int msat::ctx_create(msat_ctx **out, int32_t n_vars, int64_t n_clauses, const in
     if (block_rows) {
         const int rrc = build_block_rows(n_vars, m, kfix, coff, lit, weights, lblk, ro);
         if (rrc) return rrc;
-        occ_to_rows(occ, ro);
     }
+    scatter_occurrences(n_vars, m, hc, block_rows ? &ro.row : nullptr);
     std::vector<int2> occx;
     if (expand) {
         occx.resize((size_t)nnz);

@@ -244,16 +244,26 @@ int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits
         }
     });
     out.voff[(size_t)n] = (int32_t)rtot[(size_t)Tt];
-    out.occ.alloc((size_t)out.nnz);
-    parallel_ranges(m, Tt, [&](int t, int64_t b, int64_t e) {
-        int32_t *c = cnt.get() + (size_t)t * n;
-        for (int64_t j = b; j < e; ++j)
-            for (int32_t p = out.coff[(size_t)j]; p < out.coff[(size_t)j + 1]; ++p) {
-                const int32_t L = out.lit[(size_t)p];
-                out.occ[(size_t)c[L >> 1]++] = (int32_t)(j << 1) | (L & 1);
-            }
-    });
+    // every thread's first slot per variable, for scatter_occurrences
+    out.slots = std::move(cnt);
+    out.slot_threads = Tt;
     return MSAT_OK;
+}
+
+void scatter_occurrences(int32_t n, int64_t m, HostCnf &hc, const I32Buf *row) {
+    const int Tt = hc.slot_threads;
+    hc.occ.alloc((size_t)hc.nnz);
+    parallel_ranges(m, Tt, [&](int t, int64_t b, int64_t e) {
+        int32_t *c = hc.slots.get() + (size_t)t * n;
+        for (int64_t j = b; j < e; ++j) {
+            const int32_t r = row ? (*row)[(size_t)j] : (int32_t)j;
+            for (int32_t p = hc.coff[(size_t)j]; p < hc.coff[(size_t)j + 1]; ++p) {
+                const int32_t L = hc.lit[(size_t)p];
+                hc.occ[(size_t)c[L >> 1]++] = (r << 1) | (L & 1);
+            }
+        }
+    });
+    hc.slots.reset();
 }
 
 }  // namespace msat
@@ -339,16 +349,6 @@ int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, con
         });
     }
     return MSAT_OK;
-}
-
-void occ_to_rows(I32Buf &occ, const RowOrder &ro) {
-    const int64_t nnz = (int64_t)occ.size();
-    parallel_ranges(nnz, threads_for(nnz), [&](int, int64_t b, int64_t e) {
-        for (int64_t q = b; q < e; ++q) {
-            const int32_t o = occ[(size_t)q];
-            occ[(size_t)q] = (ro.row[(size_t)(o >> 1)] << 1) | (o & 1);
-        }
-    });
 }
 
 }  // namespace msat

@@ -41,12 +41,17 @@ struct HostCnf {
     int64_t wsum = 0;           // total clause weight
     int32_t max_len = 0, max_deg = 0;
     int32_t kfix = 0;           // common clause length, or 0
+    // between build_host_cnf and scatter_occurrences: thread t's first
+    // occurrence slot of variable i at [t * n + i]
+    std::unique_ptr<int32_t[]> slots;
+    int slot_threads = 0;
 };
 
 // Checks the caller's arrays (offsets non-decreasing from 0, literals in
 // range, weights >= 1, canonical clauses of at most kMaxClauseLen literals)
-// and fills `out`; MSAT_EINVAL with the message of the first violation in
-// input order.  The work is spread over the host's hardware threads.
+// and fills `out` up to the occurrence offsets (voff); MSAT_EINVAL with the
+// message of the first violation in input order.  The work is spread over
+// the host's hardware threads.
 int build_host_cnf(int32_t n, int64_t m, const int64_t *off, const int32_t *lits, const int64_t *w,
                    HostCnf &out);
 
@@ -66,7 +71,9 @@ struct RowOrder {
 int build_block_rows(int32_t n, int64_t m, int32_t kfix, const I32Buf &coff, const I32Buf &lit,
                      const int64_t *w, const std::vector<int2> &lblk, RowOrder &ro);
 
-// Occurrence words clause << 1 | neg become row << 1 | neg.
-void occ_to_rows(I32Buf &occ, const RowOrder &ro);
+// The occurrence list (transposed CSR, each variable's occurrences in
+// (clause, position) order): words row << 1 | neg, with row = row[j] of
+// clause j when `row` is given (the grouped store), else j.
+void scatter_occurrences(int32_t n, int64_t m, HostCnf &hc, const I32Buf *row);
 
 }  // namespace msat
