@@ -31,9 +31,11 @@
 // the bits to be read out.
 //
 // Schedule: with more tiles than SMs, every CTA of a one-per-SM grid takes
-// the same number of whole tiles, and when the leftover tiles would fill at
-// most half a wave they are split instead, each into `split` equal k-step
-// pieces on as many CTAs.  Every term of S_jb is -1, 0 or +1, so S_jb =
+// the same number of whole tiles back to back; leftover tiles that would
+// fill at most half a wave are split, each into `split` equal k-step pieces
+// on as many CTAs (which take their piece first), and a larger leftover
+// runs as one more whole tile on the first CTAs.  Every term of S_jb is -1,
+// 0 or +1, so S_jb =
 // -len_j exactly when, in every piece, the piece's partial sum equals minus
 // the number of the clause's literals whose variable lies in the piece's
 // k-range.  A piece therefore tests its own partial sums against those
