@@ -149,6 +149,13 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Programmatic dependent launch: the evaluator is launched to overlap the
+// kernel that packs its assignment operand; it waits for that kernel (and
+// the visibility of its writes) before its first read of the packed batch
+// or write of the costs.  The packing kernels let it start at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Named barrier of the eight epilogue warps (256 threads).
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
@@ -399,6 +406,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             const DenseSeg g = seg_at(d, cta, j);
             const int m0 = (g.tile % d.tiles_m) * kTM, n0 = (g.tile / d.tiles_m) * ntile;
             for (int kt = g.ka; kt < g.kb && kt < g.ka + kPrefetch; ++kt) tma_prefetch_2d(&tmA, kt * kRowBytes, m0);
+            if (j == 0) grid_dep_wait();  // the clause tiles above need nothing from the packing kernel
             for (int kt = g.ka; kt < g.kb; ++kt) {
                 const int s = it % kStages;
                 if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kRowBytes, m0);
@@ -475,6 +483,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         const int h = (warp - 2) >> 2;
         const int r = 32 * q + lane;  // row within the tile
         const int etid = threadIdx.x - 64;
+        grid_dep_wait();  // the costs were cleared by the packing kernel
         for (int j = 0; j < nseg; ++j) {
             const DenseSeg g = seg_at(d, cta, j);
             const int buf = j % nbuf;
@@ -756,6 +765,7 @@ __device__ __forceinline__ void pack_transpose(const T *__restrict__ src, int n,
 // From the caller's int8 [n][nb] batch (> 0 is true).
 __global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uint8_t *__restrict__ Xt,
                                 int n_pad, int rows) {
+    grid_dep_launch();
     pack_transpose<int8_t>(a, n, nb, Xt, n_pad, rows);
 }
 
@@ -763,6 +773,7 @@ __global__ void k_dense_convert(const int8_t *__restrict__ a, int n, int nb, uin
 // as +1, otherwise -1 -- the rounding of Sec. 4 -- without the int8 copy.
 __global__ void k_dense_convert_x(const float *__restrict__ x, int n, int nb, uint8_t *__restrict__ Xt,
                                   int n_pad, int rows, long long *__restrict__ cost) {
+    grid_dep_launch();
     if (blockIdx.x == 0 && blockIdx.y == 0)  // the GEMM that follows in stream order adds into cost
         for (int b = threadIdx.y * 32 + threadIdx.x; b < nb; b += 32 * blockDim.y) cost[b] = 0;
     pack_transpose<float>(x, n, nb, Xt, n_pad, rows);
@@ -897,10 +908,21 @@ cudaError_t launch_dense_gemm(const DenseDev &d, int nb, long long *cost, cudaSt
     const DenseSched p = dense_plan(d, ntile, &grid);
     if (p.tail > 0 && (p.tail * p.split > d.ptgt_slots || p.tail > d.part_cnts || ntile != d.pmask_ntile))
         return cudaErrorInvalidValue;
-    k_dense_eval<<<grid, kDenseThreads, smem, st>>>(d.tmA, d.tmB, d.target, d.wgt, d.unit_w ? 1 : 0, p, tmem_cols,
-                                                   nb, reinterpret_cast<unsigned long long *>(cost), d.ptgt,
-                                                   d.pmask, d.part_cnt, d.errflag);
-    return cudaGetLastError();
+    // launched to overlap the packing kernel before it in the stream (it
+    // waits for that kernel's writes where it needs them)
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kDenseThreads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_dense_eval, d.tmA, d.tmB, d.target, d.wgt, d.unit_w ? 1 : 0, p, tmem_cols, nb,
+                              reinterpret_cast<unsigned long long *>(cost), d.ptgt, d.pmask, d.part_cnt,
+                              d.errflag);
 }
 
 size_t smem_max_dense() { return dense_smem_bytes(256); }
