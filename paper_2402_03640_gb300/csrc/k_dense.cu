@@ -70,7 +70,7 @@ constexpr int kSfCols = 32;         // TMEM columns of scale factors (A: first 1
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;  // four ue8m0 scale factors of 2^0
 constexpr int kStages = 4;
 constexpr int kAccBufs = 2;         // TMEM accumulators at most (segment j uses j % bufs)
-constexpr int kPrefetch = 6;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
+constexpr int kPrefetch = 1;        // clause-matrix k-tiles prefetched into L2 ahead of their loads
 constexpr int kDenseThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per lane quarter)
 constexpr int kEpiWarps = 8;
 constexpr int kHeader = 4096;       // barriers, TMEM address, column sums
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             if (j == 0) grid_dep_wait();  // the clause tiles above need nothing from the packing kernel
             for (int kt = g.ka; kt < g.kb; ++kt) {
                 const int s = it % kStages;
-                if (kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kRowBytes, m0);
+                if (kPrefetch > 0 && kt + kPrefetch < g.kb) tma_prefetch_2d(&tmA, (kt + kPrefetch) * kRowBytes, m0);
                 if (it >= kStages) {
                     const uint32_t parity = (uint32_t)((it / kStages - 1) & 1);
                     if (*(volatile int *)&H->abort || !mbar_wait(&H->empty[s], parity, 0, kWaitNs)) {
