@@ -86,3 +86,19 @@ def test_piece_targets_at_k_step_boundaries():
         bounds = [min(n, (p * kt // split) * 256) for p in range(split + 1)]
         bounds[-1] = n
         assert np.array_equal(_pieces_test(clauses, n, a01, bounds), want), split
+
+
+def test_piece_targets_up_to_eight_pieces():
+    """Up to eight pieces of whole 256-variable k-steps (the most the
+    evaluator splits a tile into), on an instance with 20 k-steps."""
+    rng = np.random.default_rng(9)
+    n = 5000
+    kt = (n + 255) // 256
+    cnf = uniform_ksat(n, 400, 3, seed=8)
+    clauses = [_canonical(c) for c in cnf.clauses()] + [list(range(1, n + 1, 97)), [], [17, -17, 4000]]
+    a01 = rng.integers(0, 2, size=(24, n)).astype(np.uint8)
+    want = _unsat_by_definition(clauses, a01)
+    for split in (5, 6, 7, 8):
+        bounds = [min(n, (p * kt // split) * 256) for p in range(split + 1)]
+        bounds[-1] = n
+        assert np.array_equal(_pieces_test(clauses, n, a01, bounds), want), split
